@@ -1,0 +1,149 @@
+"""FPW oracle: plain FP64 CPU implementation of Eq. 1 (Section 2) of
+Finkbeiner, Prince & Whitebook, "A Fast Periodicity Detection Algorithm
+Sensitive to Arbitrary Waveforms" (arXiv:2502.00243).
+
+TEST INFRASTRUCTURE ONLY. Only ``tests/``, ``__graft_entry__.smoke()`` and
+``bench.py``'s CPU-baseline / reference leg may import this package. It shares
+no code with the CUDA library under ``paper_2502_00243_gb300/`` and never
+imports it.
+
+The arithmetic lives in ``fpw_oracle.c`` (binary64, built with
+``-ffp-contract=off`` so every operation rounds exactly as written on x86 and
+Arm alike). This module only compiles it with the system C compiler and
+marshals numpy arrays through ctypes.
+
+Functions and the passages they follow:
+
+* :func:`fpw` -- Eq. 1 for one light curve at every trial frequency, bins from
+  Appendix A.1 (m = floor(M * frac(t f)), t_ref = 0), sums from Appendix A.4.
+* :func:`fpw_batch` -- the same for a ragged batch (CSR offsets), threads over
+  curves, optional dense S and per-curve top-k peaks (Section 3.5
+  post-processing).
+* :func:`topk` -- the k highest local maxima of a periodogram (Section 3.5).
+* :func:`bins` -- bin of every (frequency, observation) pair and the exact
+  distance from t*f to the nearest bin edge, for bin-mismatch accounting.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "fpw_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle_fpw.so")
+_lock = threading.Lock()
+_lib = None
+
+STATUS = {0: "ok", 1: "invalid argument", 2: "invalid data", 3: "out of memory"}
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def build(force: bool = False) -> str:
+    """Compile ``fpw_oracle.c`` into ``liboracle_fpw.so`` next to it."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    cc = os.environ.get("CC", "gcc")
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = [cc, "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-pthread",
+           _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB)
+            d, i64, c_int = ctypes.c_double, ctypes.c_int64, ctypes.c_int
+            vp = ctypes.c_void_p
+            lib.oracle_fpw.argtypes = [vp, vp, vp, i64, vp, i64, c_int, d, vp]
+            lib.oracle_fpw.restype = c_int
+            lib.oracle_fpw_batch.argtypes = [vp, i64, vp, vp, vp, vp, i64, c_int, d, c_int, vp, c_int, c_int, vp, vp]
+            lib.oracle_fpw_batch.restype = c_int
+            lib.oracle_topk.argtypes = [vp, i64, c_int, c_int, vp, vp]
+            lib.oracle_topk.restype = c_int
+            lib.oracle_bins.argtypes = [vp, i64, vp, i64, c_int, vp, vp]
+            lib.oracle_bins.restype = c_int
+            lib.oracle_version.restype = c_int
+            _lib = lib
+    return _lib
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+def _check(rc: int) -> None:
+    if rc != 0:
+        raise OracleError(f"oracle status {rc}: {STATUS.get(rc, 'unknown')}")
+
+
+def fpw(t, x, sigma, freqs, M: int, inv_alpha2: float = 0.0) -> np.ndarray:
+    """S_FPW (Eq. 1) of one curve at every frequency in ``freqs`` (float64)."""
+    lib = _load()
+    t, x, sigma, freqs = _f64(t), _f64(x), _f64(sigma), _f64(freqs)
+    n = t.shape[0]
+    if x.shape[0] != n or sigma.shape[0] != n:
+        raise ValueError("t, x, sigma must have equal length")
+    S = np.empty(freqs.shape[0], dtype=np.float64)
+    _check(lib.oracle_fpw(_ptr(t), _ptr(x), _ptr(sigma), n, _ptr(freqs), freqs.shape[0], int(M), float(inv_alpha2),
+                          _ptr(S)))
+    return S
+
+
+def fpw_batch(offsets, t, x, sigma, freqs, M: int, inv_alpha2: float = 0.0, *, nthreads: int | None = None,
+              dense: bool = True, k: int = 0, raw: bool = False):
+    """Ragged batch. Returns ``(S, topk_idx, topk_S)``; ``S`` is ``[C, F]`` or None."""
+    lib = _load()
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    t, x, sigma, freqs = _f64(t), _f64(x), _f64(sigma), _f64(freqs)
+    C = offsets.shape[0] - 1
+    F = freqs.shape[0]
+    if nthreads is None:
+        nthreads = os.cpu_count() or 1
+    S = np.empty((C, F), dtype=np.float64) if dense else None
+    idx = np.empty((C, max(k, 0)), dtype=np.int32)
+    val = np.empty((C, max(k, 0)), dtype=np.float64)
+    _check(lib.oracle_fpw_batch(_ptr(offsets), C, _ptr(t), _ptr(x), _ptr(sigma), _ptr(freqs), F, int(M),
+                                float(inv_alpha2), int(nthreads), _ptr(S), int(k), int(bool(raw)),
+                                _ptr(idx) if k > 0 else None, _ptr(val) if k > 0 else None))
+    return S, idx, val
+
+
+def topk(S, k: int, raw: bool = False):
+    """Top-k peaks (or raw top-k) of one periodogram: ``(idx int32[k], S float64[k])``."""
+    lib = _load()
+    S = _f64(S)
+    idx = np.empty(k, dtype=np.int32)
+    val = np.empty(k, dtype=np.float64)
+    _check(lib.oracle_topk(_ptr(S), S.shape[0], int(k), int(bool(raw)), _ptr(idx), _ptr(val)))
+    return idx, val
+
+
+def bins(t, freqs, M: int, *, want_bins: bool = True, want_edge: bool = True):
+    """Bins ``int32[F, n]`` and exact edge distances ``float64[F, n]`` (cycles)."""
+    lib = _load()
+    t, freqs = _f64(t), _f64(freqs)
+    n, F = t.shape[0], freqs.shape[0]
+    b = np.empty((F, n), dtype=np.int32) if want_bins else None
+    e = np.empty((F, n), dtype=np.float64) if want_edge else None
+    _check(lib.oracle_bins(_ptr(t), n, _ptr(freqs), F, int(M), _ptr(b), _ptr(e)))
+    return b, e
+
+
+def version() -> int:
+    return int(_load().oracle_version())
