@@ -1,0 +1,459 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the GB300 FPW periodogram.
+
+Workload (one "step" = one pass of the whole hot path over one batch): the
+10^5-curve sweep -- curves with N log-uniform in [100, 3000] and ZTF-like
+cadence, mixed waveforms, M phase bins (default 20), 5*10^5 linear trial
+frequencies 0.01-50 1/d, per-curve top-5 peaks -- split into ten batches of
+10^4 curves; step s processes batch (s * world + rank) mod 10, so the default
+ten timed steps on one GPU cover the whole sweep once. Inputs are synthetic
+(seeded) and larger than L2 per batch.
+
+Reported: evaluations (observation x frequency pairs) per second for the whole
+job, the tile kernel's roofline fraction, an end-to-end number through the
+host-buffer C entry point, the FP64 CPU oracle on a bounded sample
+(cpu_baseline), and the plain binary64 one-curve-per-launch GPU form on a
+stratified curve sample.
+
+--impl reference times the FP64 CPU oracle instead (each step a bounded sample
+of the same workload).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "obs×freq FPW evals/s on 1 GB300 (batched split-prec vs plain FP64), % roofline"
+UNIT = "evals/s"
+WORKLOAD = "sweep_100k"
+NSM_NOMINAL = 152
+SM_MAX_MHZ_NOMINAL = 2070.0
+SMEM_EVALS_PER_CLK_SM = 8  # 16 B (A, B) read-modify-write per evaluation at 128 B/clk/SM
+
+
+# ---------------------------------------------------------------- workload generation (spawned workers)
+def _gen_chunk(args):
+    lo, hi, M = args
+    import lightcurves as L
+    w = L.make(WORKLOAD, range(lo, hi), M=M, nfreq=2)
+    return lo, w.offsets, w.t, w.x, w.sigma
+
+
+def make_batches(batch_ids, batch_curves, M, workers):
+    """Host arrays for each batch id: dict b -> (offsets, t, x, sigma)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+
+    import numpy as np
+    chunk = 500
+    tasks = []
+    for b in batch_ids:
+        for lo in range(b * batch_curves, (b + 1) * batch_curves, chunk):
+            tasks.append((lo, min(lo + chunk, (b + 1) * batch_curves), M))
+    parts = {}
+    if workers > 1:
+        with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+            for lo, off, t, x, s in ex.map(_gen_chunk, tasks):
+                parts[lo] = (off, t, x, s)
+    else:
+        for tsk in tasks:
+            lo, off, t, x, s = _gen_chunk(tsk)
+            parts[lo] = (off, t, x, s)
+    out = {}
+    for b in batch_ids:
+        los = list(range(b * batch_curves, (b + 1) * batch_curves, chunk))
+        offs, ts, xs, ss, base = [np.zeros(1, dtype=np.int64)], [], [], [], 0
+        for lo in los:
+            off, t, x, s = parts[lo]
+            offs.append(off[1:] + base)
+            base += int(off[-1])
+            ts.append(t)
+            xs.append(x)
+            ss.append(s)
+        out[b] = (np.concatenate(offs), np.concatenate(ts), np.concatenate(xs), np.concatenate(ss))
+    return out
+
+
+def stratified(offsets, count):
+    """Curve indices spread evenly over the batch sorted by size."""
+    import numpy as np
+    n = offsets[1:] - offsets[:-1]
+    order = np.argsort(n, kind="stable")
+    pick = np.linspace(0, len(order) - 1, min(count, len(order))).round().astype(int)
+    return np.sort(order[pick])
+
+
+def subset(batch, ids):
+    import numpy as np
+    off, t, x, s = batch
+    parts = [(off[i], off[i + 1]) for i in ids]
+    o = np.zeros(len(ids) + 1, dtype=np.int64)
+    o[1:] = np.cumsum([b - a for a, b in parts])
+    cat = lambda arr: np.concatenate([arr[a:b] for a, b in parts]) if parts else np.zeros(0)
+    return o, cat(t), cat(x), cat(s)
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [v.strip() for v in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+# ---------------------------------------------------------------- helpers
+def env_rank():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def sm_max_mhz():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh).get("sm_max_mhz", SM_MAX_MHZ_NOMINAL))
+    except (OSError, ValueError):
+        return SM_MAX_MHZ_NOMINAL
+
+
+def config_block(args, nbatches, batch_evals_mean):
+    return {"workload": f"{WORKLOAD}: 1e5 ZTF-like curves, N log-uniform 100-3000, mixed waveforms, M={args.M}, "
+                        f"5e5 linear freqs 0.01-50 1/d, top-{args.k}; one step = one batch of {args.batch_curves} "
+                        f"curves ({nbatches} batches)",
+            "curves_per_step": args.batch_curves, "nfreq": 500_000, "M": args.M, "k": args.k,
+            "phase": "fixed64 (exact integer anchor + 64-bit stepping)", "bin_sums": "f32",
+            "evals_per_step_mean": batch_evals_mean,
+            "l2": "inputs larger than L2 (>= 200 MB of float64 per batch, distinct batch each step)"}
+
+
+def oracle_rate(batch, ids, F_grid, M, k, nthreads):
+    import numpy as np
+
+    import oracle
+    o, t, x, s = subset(batch, ids)
+    t0 = time.perf_counter()
+    oracle.fpw_batch(o, t, x, s, F_grid, M, dense=False, k=k, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    ev = float(o[-1]) * F_grid.shape[0]
+    return ev, dt
+
+
+def oracle_sample(batch, F_grid, M, k, target_s, cores):
+    """A bounded oracle sample: `cores` curves stratified by N (one per thread)
+    and a contiguous slice of the frequency grid sized for about target_s."""
+    ids = stratified(batch[0], cores)
+    o = subset(batch, ids)[0]
+    probe_F = F_grid[: max(1000, F_grid.shape[0] // 100)]
+    ev, dt = oracle_rate(batch, ids, probe_F, M, k, cores)
+    rate = ev / max(dt, 1e-6)
+    nf = int(max(1000, min(F_grid.shape[0], target_s * rate / max(float(o[-1]), 1.0))))
+    start = (F_grid.shape[0] - nf) // 2
+    return ids, F_grid[start:start + nf]
+
+
+# ---------------------------------------------------------------- reference arm: the CPU oracle
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return 0
+    import numpy as np
+
+    import lightcurves as L
+    cores = os.cpu_count() or 1
+    nb = args.curves_total // args.batch_curves
+    steps = args.warmup + args.steps
+    ids = sorted({s % nb for s in range(steps)})
+    batches = make_batches(ids, args.batch_curves, args.M, workers=min(cores, 16))
+    F_grid = L.freq_grid(WORKLOAD)
+    _, F_s = oracle_sample(batches[ids[0]], F_grid, args.M, args.k, args.ref_step_seconds, cores)
+    total_ev, total_t = 0.0, 0.0
+    for s in range(steps):
+        b = batches[s % nb]
+        pick = stratified(b[0], cores)
+        ev, dt = oracle_rate(b, pick, F_s, args.M, args.k, cores)
+        if s >= args.warmup:
+            total_ev += ev
+            total_t += dt
+    value = total_ev / total_t
+    sample = (f"{cores} curves per step (one per core), stratified by N from the step's {args.batch_curves}-curve "
+              f"batch, x the central {F_s.shape[0]} of the 5e5 grid frequencies, M={args.M}, top-{args.k}")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(config_block(args, nb, None), phase="binary64 fl(t f)", bin_sums="f64"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_gb300(args):
+    import numpy as np
+    import torch
+
+    import lightcurves as L
+    rank, world, local_rank = env_rank()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_
+        dist = dist_
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    else:
+        torch.cuda.set_device(local_rank)
+    import paper_2502_00243_gb300 as G
+    G.lib()  # fail loudly if the library is missing
+
+    cores = os.cpu_count() or 1
+    nb = args.curves_total // args.batch_curves
+    steps = args.warmup + args.steps
+    batch_of = [(s * world + rank) % nb for s in range(steps)]
+    ids = sorted(set(batch_of))
+    workers = max(1, min(16, cores // max(1, min(world, cores))))
+    t_gen = time.perf_counter()
+    host = make_batches(ids, args.batch_curves, args.M, workers=workers)
+    t_gen = time.perf_counter() - t_gen
+    F_grid = L.freq_grid(WORKLOAD)
+    F = F_grid.shape[0]
+    dev = {b: dict(offsets=torch.from_numpy(h[0]).cuda(), t=torch.from_numpy(h[1]).cuda(),
+                   x=torch.from_numpy(h[2]).cuda(), sigma=torch.from_numpy(h[3]).cuda()) for b, h in host.items()}
+    freqs = torch.from_numpy(F_grid).cuda()
+    C, k = args.batch_curves, args.k
+    idx = torch.empty(C * k, dtype=torch.int32, device="cuda")
+    Sk = torch.empty(C * k, dtype=torch.float32, device="cuda")
+    ctx = G.Context(local_rank)
+    params = G.fpw_params_default()
+    stream = torch.cuda.current_stream()
+
+    def step(s):
+        b = batch_of[s]
+        d = dev[b]
+        G.fpw_periodogram_batch_ex(ctx, stream, params, d["offsets"], host[b][0], d["t"], d["x"], d["sigma"], freqs,
+                                   args.M, k, idx, Sk)
+        return float(host[b][0][-1]) * F
+
+    for s in range(args.warmup):
+        step(s)
+    torch.cuda.synchronize()
+    if ctx.status() != 0:
+        raise RuntimeError("device status error during warm-up")
+    ctx.set_timing(True)
+    ctx.kernel_time()
+    clocks = ClockSampler(local_rank) if rank == 0 else None
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    evals = 0.0
+    for s in range(args.warmup, steps):
+        evals += step(s)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop() if clocks else None
+    ms = e0.elapsed_time(e1)
+    kern_ms, launches = ctx.kernel_time()
+    ctx.set_timing(False)
+    status = ctx.status()
+    if status != 0:
+        raise RuntimeError(f"device status {status} in the timed region")
+    if dist:
+        tt = torch.tensor([ms, evals, kern_ms], dtype=torch.float64, device="cuda")
+        mx = tt.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tt, op=dist.ReduceOp.SUM)
+        ms_max, evals_all = float(mx[0]), float(tt[1])
+    else:
+        ms_max, evals_all = ms, evals
+    value = evals_all / (ms_max / 1e3)
+
+    # ---- end to end through the host-buffer entry point (pinned host memory)
+    e2e = None
+    if not args.no_e2e:
+        pinned = {}
+        for b in ids:
+            arrs = []
+            for a in host[b]:
+                p = torch.empty(a.shape, dtype=torch.from_numpy(a).dtype, pin_memory=True)
+                p.numpy()[...] = a
+                arrs.append(p)
+            pinned[b] = arrs
+        fp = torch.empty(F, dtype=torch.float64, pin_memory=True)
+        fp.numpy()[...] = F_grid
+        oi = torch.empty(C * k, dtype=torch.int32, pin_memory=True)
+        os_ = torch.empty(C * k, dtype=torch.float32, pin_memory=True)
+
+        def hstep(s):
+            b = batch_of[s]
+            o, t, x, sg = (p.numpy() for p in pinned[b])
+            G.fpw_periodogram_batch_host(ctx, params, o, t, x, sg, fp.numpy(), args.M, k, oi.numpy(), os_.numpy())
+            return float(o[-1]) * F, 8 * (o.size + 3 * t.size + F), 8 * C * k
+
+        for s in range(min(args.warmup, 2)):
+            hstep(s)
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        ev_h, h2d, d2h = 0.0, 0, 0
+        for s in range(args.warmup, steps):
+            e_, hb, db = hstep(s)
+            ev_h += e_
+            h2d += hb
+            d2h += db
+        dt = time.perf_counter() - t0
+        if dist:
+            tt = torch.tensor([dt, ev_h], dtype=torch.float64, device="cuda")
+            mx = tt.clone()
+            dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+            dist.all_reduce(tt, op=dist.ReduceOp.SUM)
+            dt, ev_h = float(mx[0]), float(tt[1])
+        e2e = {"value": ev_h / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d // args.steps),
+               "d2h_bytes_per_step": int(d2h // args.steps), "api": "fpw_periodogram_batch_host"}
+
+    # ---- plain binary64 one-curve-per-launch GPU form, stratified sample
+    plain = None
+    if not args.no_plain:
+        b0 = ids[0]
+        pick = stratified(host[b0][0], args.plain_curves)
+        o, t, x, sg = subset(host[b0], pick)
+        dp = [torch.from_numpy(a).cuda() for a in (o, t, x, sg)]
+        pi = torch.empty(len(pick) * k, dtype=torch.int32, device="cuda")
+        ps = torch.empty(len(pick) * k, dtype=torch.float32, device="cuda")
+        pp = G.fpw_params_default(phase_mode=G.FPW_PHASE_FP64)
+        G.fpw_periodogram_batch_ex(ctx, stream, pp, dp[0], o, dp[1], dp[2], dp[3], freqs, args.M, k, pi, ps)
+        torch.cuda.synchronize()
+        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        q0.record(stream)
+        G.fpw_periodogram_batch_ex(ctx, stream, pp, dp[0], o, dp[1], dp[2], dp[3], freqs, args.M, k, pi, ps)
+        q1.record(stream)
+        torch.cuda.synchronize()
+        pev = float(o[-1]) * F
+        pval = pev / (q0.elapsed_time(q1) / 1e3)
+        # the split-precision batched kernel on the same sample, for a like-for-like ratio
+        G.fpw_periodogram_batch_ex(ctx, stream, params, dp[0], o, dp[1], dp[2], dp[3], freqs, args.M, k, pi, ps)
+        torch.cuda.synchronize()
+        plain = {"value": pval, "unit": UNIT, "sample": f"{len(pick)} curves stratified by N from batch {b0}, "
+                 f"full grid, M={args.M}, one launch per curve (+1 top-k launch)",
+                 "speedup_of_batched_split": value / pval}
+
+    # ---- CPU oracle on a bounded sample (rank 0, one GPU only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        b0 = ids[0]
+        pick, F_s = oracle_sample(host[b0], F_grid, args.M, k, args.cpu_seconds, cores)
+        ev, dt = oracle_rate(host[b0], pick, F_s, args.M, k, cores)
+        cpu = {"value": ev / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{len(pick)} curves (one per core) stratified by N from batch {b0} x the central "
+                         f"{F_s.shape[0]} grid frequencies, M={args.M}, top-{k} ({ev:.3g} evals in {dt:.1f} s)"}
+
+    if rank == 0:
+        nsm = torch.cuda.get_device_properties(local_rank).multi_processor_count
+        peak = nsm * sm_max_mhz() * 1e6 * SMEM_EVALS_PER_CLK_SM / 1e9
+        achieved = evals / (kern_ms / 1e3) / 1e9 if kern_ms > 0 else None
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Geval/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "kernel": "tile_kernel<R=4, fixed64, f32>", "launches": launches,
+                "kernel_ms_avg": kern_ms / max(launches, 1),
+                "peak_basis": f"shared-memory pipe: one 8 B load + one 8 B store of the (A,B) bin pair per "
+                              f"evaluation at 128 B/clk/SM -> {SMEM_EVALS_PER_CLK_SM} evals/clk/SM x {nsm} SMs x "
+                              f"{sm_max_mhz():.0f} MHz (recipe unit counts and max clock)"}
+        mean_ev = float(np.mean([float(host[b][0][-1]) * F for b in ids]))
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": config_block(args, nb, mean_ev), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": 4 * args.steps, "clocks": clk, "plain_fp64": plain,
+                "gen_seconds": round(t_gen, 2)}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--M", type=int, default=20)
+    ap.add_argument("--k", type=int, default=5)
+    ap.add_argument("--batch-curves", type=int, default=10_000)
+    ap.add_argument("--curves-total", type=int, default=100_000)
+    ap.add_argument("--plain-curves", type=int, default=32)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-step-seconds", type=float, default=3.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 0 or args.steps < 1:
+        ap.error("need --steps >= 1 and --warmup >= 0")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gb300(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,188 @@
+/*
+ * fpw.h -- C ABI of the GB300 FPW periodogram library (libfpw_gb300.so).
+ *
+ * Fast Periodicity Weighting (Finkbeiner, Prince & Whitebook,
+ * arXiv:2502.00243). For a light curve with observation times t_i, fluxes x_i
+ * and errors sigma_i, and a trial frequency f, the library evaluates Eq. 1
+ * (Section 2, eq:phasesum):
+ *
+ *     w_i  = 1 / sigma_i^2,                 a_i = x_i w_i
+ *     m_i  = floor(M * frac(t_i f))         (Appendix A.1 phase bin, t_ref = 0,
+ *                                            zero-indexed 0..M-1)
+ *     A_m  = sum_{i: m_i = m} a_i,          B_m = sum_{i: m_i = m} w_i
+ *     S(f) = sum_m A_m^2 / (B_m + 1/alpha^2)
+ *
+ * for every (light curve, trial frequency) pair, and the post-processing step
+ * of Section 3.5 (the highest peaks of each periodogram).
+ *
+ * Conventions shared by every entry point:
+ *  - Arrays are caller-owned. Unless an entry point says "host", every pointer
+ *    is a DEVICE pointer on the context's device (e.g. a torch CUDA tensor's
+ *    data_ptr()). The library never frees caller memory.
+ *  - Times are used as given (t_ref = 0): subtract a reference epoch first if
+ *    |t f| would exceed about 2^40 cycles. Fluxes are used as given: the
+ *    library does not subtract the mean (Section 3.5 calls that
+ *    pre-processing, not part of FPW).
+ *  - A bin whose denominator B_m + 1/alpha^2 is 0 (an empty bin with
+ *    1/alpha^2 = 0) contributes 0. Bins are half-open [m/M, (m+1)/M).
+ *  - A peak is a local maximum S_k > S_{k-1} and S_k >= S_{k+1}, with
+ *    out-of-range neighbours taken as -infinity; peaks are ranked by S
+ *    descending, ties to the lower frequency index. Missing peaks are reported
+ *    as index -1 and S = NaN.
+ *  - Return value: FPW_OK (0) or one of the FPW_E* codes below. No C++
+ *    exception crosses this ABI. Entry points without the _ex suffix are
+ *    synchronous and report data errors directly; _ex entry points are
+ *    stream-ordered and latch device-detected data errors in the context,
+ *    reported by fpw_ctx_status().
+ */
+#ifndef FPW_GB300_H
+#define FPW_GB300_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__) || defined(__clang__)
+#define FPW_API __attribute__((visibility("default")))
+#else
+#define FPW_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FPW_OK 0
+#define FPW_EINVAL 1   /* bad argument: null pointer, M < 1, negative size, bad offsets, k out of range */
+#define FPW_EDATA 2    /* sigma <= 0 or a non-finite t, x, sigma or frequency (found on the device) */
+#define FPW_ENOMEM 3   /* device or host allocation failed */
+#define FPW_ECUDA 4    /* a CUDA runtime call failed */
+#define FPW_ETIMEOUT 5 /* a bounded device-side wait gave up */
+#define FPW_ENOTSUP 6  /* combination of options not supported */
+
+/* Phase arithmetic (how frac(t f) is formed on the device). */
+#define FPW_PHASE_FIXED64 0 /* default: exact integer product of the binary64 significands of t and the
+                               anchor frequency, then 64-bit fixed-point stepping across the grid */
+#define FPW_PHASE_FP64 1    /* plain form: fl(t f) - floor(fl(t f)) in binary64 per evaluation,
+                               binary64 bin sums, one launch per curve */
+#define FPW_PHASE_FP32 2    /* FP32 phase: anchor rounded to FP32 every K frequencies, FP32 steps */
+
+#define FPW_ACCUM_FP32 0 /* bin sums A_m, B_m in FP32 (default) */
+#define FPW_ACCUM_FP64 1 /* bin sums in binary64 */
+
+#define FPW_PEAK_LOCALMAX 0 /* top-k over local maxima of S (default) */
+#define FPW_PEAK_RAW 1      /* top-k over every frequency */
+
+#define FPW_MAX_TOPK 64 /* largest k accepted by the batched calls */
+
+typedef struct fpw_ctx fpw_ctx; /* opaque: device, scratch buffers, plan and graph caches */
+
+typedef struct fpw_params {
+  double inv_alpha2;    /* 1/alpha^2 >= 0 in Eq. 1's denominator (default 0: the prior is neglected) */
+  int phase_mode;       /* FPW_PHASE_* (default FPW_PHASE_FIXED64) */
+  int accum;            /* FPW_ACCUM_* (default FPW_ACCUM_FP32) */
+  int K;                /* FPW_PHASE_FP32 only: re-anchor interval in frequencies (default 256) */
+  int peak_mode;        /* FPW_PEAK_* (default FPW_PEAK_LOCALMAX) */
+  int threads;          /* 0 = tuned; else threads per block (multiple of 32, 32..512) */
+  int freqs_per_thread; /* 0 = tuned; else 2, 4 or 8 */
+  int obs_chunk;        /* 0 = tuned; else observations staged in shared memory per pass (>= 32) */
+  int use_graph;        /* 1 = capture the launch sequence in a CUDA graph and replay it on identical calls */
+} fpw_params;
+
+/* Fill *p with the defaults listed above. */
+FPW_API void fpw_params_default(fpw_params* p);
+
+/* Create a context on CUDA device `device` (>= 0). *ctx receives the handle.
+ * Errors: FPW_EINVAL (null ctx, bad device), FPW_ECUDA, FPW_ENOMEM. */
+FPW_API int fpw_ctx_create(fpw_ctx** ctx, int device);
+
+/* Synchronize the context's work, free its scratch memory and graphs. NULL is a no-op. */
+FPW_API int fpw_ctx_destroy(fpw_ctx* ctx);
+
+/* Synchronize the stream of the context's last call and return, then clear,
+ * the status latched by device-side checks (FPW_OK, FPW_EDATA or FPW_ETIMEOUT). */
+FPW_API int fpw_ctx_status(fpw_ctx* ctx);
+
+/* Single light curve, Eq. 1 at every frequency (Section 2; the frequency sweep of Section 4).
+ *   t, x, sigma: device float64[n] (times in days, fluxes, errors > 0), any order
+ *   freqs:       device float64[nfreq] trial frequencies (any values; linear grids take the fast path)
+ *   M:           number of phase bins, >= 1
+ *   S_out:       device float64[nfreq], receives S(f_k)
+ * Uses an internal per-device context, the legacy default stream and default
+ * parameters, and synchronizes before returning.
+ * Errors: FPW_EINVAL, FPW_EDATA (S_out then holds NaN), FPW_ECUDA, FPW_ENOMEM. */
+FPW_API int fpw_periodogram(const double* t, const double* x, const double* sigma, int64_t n, const double* freqs,
+                    int64_t nfreq, int M, double* S_out);
+
+/* As fpw_periodogram, on context `ctx`, stream `stream` (a cudaStream_t, NULL =
+ * legacy default stream) and parameters `params` (NULL = defaults).
+ * Stream-ordered: returns after enqueueing; data errors are latched in ctx. */
+FPW_API int fpw_periodogram_ex(fpw_ctx* ctx, void* stream, const fpw_params* params, const double* t, const double* x,
+                       const double* sigma, int64_t n, const double* freqs, int64_t nfreq, int M, double* S_out);
+
+/* Ragged batch of independent light curves with per-curve top-k peaks
+ * (Eq. 1 per curve and frequency; Section 3.5 post-processing).
+ *   offsets:       device int64[ncurves + 1], CSR offsets into t/x/sigma; offsets[0] = 0,
+ *                  non-decreasing (empty curves allowed: S = 0 everywhere)
+ *   t, x, sigma:   device float64[offsets[ncurves]]
+ *   freqs:         device float64[nfreq], one grid shared by all curves
+ *   M:             phase bins (>= 1);  k: peaks per curve (0 <= k <= min(FPW_MAX_TOPK, ...))
+ *   topk_idx:      device int32[ncurves * k], frequency indices of the peaks (row per curve)
+ *   topk_S:        device float32[ncurves * k], their S values
+ * Synchronous, internal context, default parameters.
+ * Errors: FPW_EINVAL, FPW_EDATA (bad curves get -1 / NaN), FPW_ECUDA, FPW_ENOMEM. */
+FPW_API int fpw_periodogram_batch(const int64_t* offsets, int64_t ncurves, const double* t, const double* x,
+                          const double* sigma, const double* freqs, int64_t nfreq, int M, int k, int32_t* topk_idx,
+                          float* topk_S);
+
+/* As fpw_periodogram_batch on ctx/stream/params.
+ *   offsets_host: optional HOST copy of offsets (NULL: the library copies the
+ *                 device offsets to the host, which synchronizes `stream`)
+ *   S_out:        optional device float64[ncurves * nfreq] dense periodograms (NULL: not written)
+ *   topk_idx/topk_S may be NULL when k == 0.
+ * With params->phase_mode == FPW_PHASE_FP64 the plain binary64 form runs:
+ * one launch per curve, binary64 phases and sums. */
+FPW_API int fpw_periodogram_batch_ex(fpw_ctx* ctx, void* stream, const fpw_params* params, const int64_t* offsets,
+                             const int64_t* offsets_host, int64_t ncurves, const double* t, const double* x,
+                             const double* sigma, const double* freqs, int64_t nfreq, int M, int k,
+                             int32_t* topk_idx, float* topk_S, double* S_out);
+
+/* End-to-end form with HOST buffers: copies the inputs to context-owned device
+ * memory, runs fpw_periodogram_batch_ex, copies the top-k back and
+ * synchronizes. All pointers are host pointers (pinned memory copies fastest).
+ * Same arguments and errors as fpw_periodogram_batch_ex, minus S_out. */
+FPW_API int fpw_periodogram_batch_host(fpw_ctx* ctx, const fpw_params* params, const int64_t* offsets, int64_t ncurves,
+                               const double* t, const double* x, const double* sigma, const double* freqs,
+                               int64_t nfreq, int M, int k, int32_t* topk_idx, float* topk_S);
+
+/* Diagnostic: the phase bin every observation gets at every frequency, computed
+ * with the same device phase arithmetic as the periodogram kernels
+ * (Appendix A.1 bin definition), for bin-mismatch accounting.
+ *   t:        device float64[n];  freqs: device float64[nfreq]
+ *   bins_out: device int32[nfreq * n], row per frequency
+ * For FPW_PHASE_FIXED64 / FPW_PHASE_FP32 the anchors sit at frequency indices
+ * that are multiples of params->K (FP32) or of the tile width (FIXED64). */
+FPW_API int fpw_debug_bins(fpw_ctx* ctx, void* stream, const fpw_params* params, const double* t, int64_t n,
+                   const double* freqs, int64_t nfreq, int M, int32_t* bins_out);
+
+/* Profiling hook. While enabled, the context records a pair of CUDA events on
+ * the caller's stream around every launch of the periodogram kernel (the
+ * persistent tile kernel; not in calls that use a CUDA graph).
+ * fpw_ctx_kernel_time waits for those events, returns in *ms the summed
+ * kernel time and in *launches the number of launches since the previous
+ * query, then resets both. */
+FPW_API int fpw_ctx_set_timing(fpw_ctx* ctx, int enable);
+FPW_API int fpw_ctx_kernel_time(fpw_ctx* ctx, double* ms, int64_t* launches);
+
+/* Human-readable text for a status code (static storage). */
+FPW_API const char* fpw_strerror(int status);
+
+/* Library ABI version (increments on incompatible changes). */
+FPW_API int fpw_version(void);
+
+/* Text of the last CUDA runtime error seen by the calling thread (static,
+ * thread-local storage; empty if none). */
+FPW_API const char* fpw_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FPW_GB300_H */

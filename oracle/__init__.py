@@ -74,6 +74,8 @@ def _load():
             lib.oracle_topk.restype = c_int
             lib.oracle_bins.argtypes = [vp, i64, vp, i64, c_int, vp, vp]
             lib.oracle_bins.restype = c_int
+            lib.oracle_min_edge.argtypes = [vp, i64, vp, i64, c_int, vp]
+            lib.oracle_min_edge.restype = c_int
             lib.oracle_version.restype = c_int
             _lib = lib
     return _lib
@@ -143,6 +145,39 @@ def bins(t, freqs, M: int, *, want_bins: bool = True, want_edge: bool = True):
     e = np.empty((F, n), dtype=np.float64) if want_edge else None
     _check(lib.oracle_bins(_ptr(t), n, _ptr(freqs), F, int(M), _ptr(b), _ptr(e)))
     return b, e
+
+
+def min_edge(t, freqs, M: int) -> np.ndarray:
+    """Per frequency, the smallest exact distance (cycles) from t_i * f to a bin edge."""
+    lib = _load()
+    t, freqs = _f64(t), _f64(freqs)
+    out = np.empty(freqs.shape[0], dtype=np.float64)
+    _check(lib.oracle_min_edge(_ptr(t), t.shape[0], _ptr(freqs), freqs.shape[0], int(M), _ptr(out)))
+    return out
+
+
+def _split_freqs(fn, freqs, nthreads, *args):
+    import concurrent.futures as cf
+    freqs = _f64(freqs)
+    nthreads = max(1, int(nthreads or (os.cpu_count() or 1)))
+    parts = np.array_split(np.arange(freqs.shape[0]), nthreads)
+    out = np.empty(freqs.shape[0], dtype=np.float64)
+
+    def one(ix):
+        if ix.size:
+            out[ix[0]:ix[-1] + 1] = fn(*args, freqs[ix[0]:ix[-1] + 1])
+    with cf.ThreadPoolExecutor(max_workers=nthreads) as ex:  # ctypes calls release the GIL
+        list(ex.map(one, parts))
+    return out
+
+
+def fpw_parallel(t, x, sigma, freqs, M: int, inv_alpha2: float = 0.0, nthreads: int | None = None) -> np.ndarray:
+    """:func:`fpw` with the frequency grid split across threads (same arithmetic per frequency)."""
+    return _split_freqs(lambda t_, x_, s_, f_: fpw(t_, x_, s_, f_, M, inv_alpha2), freqs, nthreads, t, x, sigma)
+
+
+def min_edge_parallel(t, freqs, M: int, nthreads: int | None = None) -> np.ndarray:
+    return _split_freqs(lambda t_, f_: min_edge(t_, f_, M), freqs, nthreads, t)
 
 
 def version() -> int:

@@ -262,6 +262,18 @@ int oracle_fpw_batch(const int64_t* offsets, int64_t ncurves, const double* t, c
 }
 
 /* ---- bins and exact edge distances (bin-mismatch accounting) ------------- */
+/* Exact distance, in cycles, from t*f to the nearest bin edge j / M. */
+static double edge_distance(double t, double f, int M) {
+  /* exact product t*f = p + e (TwoProduct via a fused multiply-add) */
+  double p = t * f;
+  double e = fma(t, f, -p);
+  double fr = p - floor(p);          /* exact: p and floor(p) share the exponent range */
+  double u = (double)M * fr;         /* M*fr = u + ue exactly */
+  double ue = fma((double)M, fr, -u);
+  double r = u - nearbyint(u);       /* exact: |u| <= M */
+  return fabs(r + (ue + (double)M * e)) / (double)M;
+}
+
 /* For each (frequency k, observation i): the oracle's bin and the exact
  * distance, in cycles, from t_i * f_k to the nearest bin edge j / M.
  * Output layout: [nfreq][n], row-major. */
@@ -272,18 +284,26 @@ int oracle_bins(const double* t, int64_t n, const double* freqs, int64_t nfreq, 
     double f = freqs[k];
     for (int64_t i = 0; i < n; ++i) {
       if (bins) bins[k * n + i] = oracle_bin(t[i], f, M);
-      if (edge_dist) {
-        /* exact product t*f = p + e (TwoProduct via a fused multiply-add) */
-        double p = t[i] * f;
-        double e = fma(t[i], f, -p);
-        double fr = p - floor(p);          /* exact: p and floor(p) share the exponent range */
-        double u = (double)M * fr;         /* M*fr = u + ue exactly */
-        double ue = fma((double)M, fr, -u);
-        double r = u - nearbyint(u);       /* exact: |u| <= M */
-        double d = fabs(r + (ue + (double)M * e)) / (double)M;
-        edge_dist[k * n + i] = d;
-      }
+      if (edge_dist) edge_dist[k * n + i] = edge_distance(t[i], f, M);
     }
+  }
+  return ORACLE_OK;
+}
+
+/* Per frequency: the smallest NONZERO exact edge distance over all
+ * observations. A frequency whose value is tiny has an observation whose bin is
+ * decided by rounding. Observations exactly on an edge (distance 0, e.g. t = 0)
+ * are skipped: there frac(t f) is a short dyadic fraction that every exact
+ * method, and binary64 for |t f| < 2^50, assigns to the upper bin. */
+int oracle_min_edge(const double* t, int64_t n, const double* freqs, int64_t nfreq, int M, double* out) {
+  if (n < 0 || nfreq < 0 || M < 1 || (nfreq > 0 && !out)) return ORACLE_EINVAL;
+  for (int64_t k = 0; k < nfreq; ++k) {
+    double best = INFINITY;
+    for (int64_t i = 0; i < n; ++i) {
+      double d = edge_distance(t[i], freqs[k], M);
+      if (d > 0.0 && d < best) best = d;
+    }
+    out[k] = best;
   }
   return ORACLE_OK;
 }

@@ -1,0 +1,214 @@
+// Internal declarations of the GB300 FPW library: kernel argument blocks,
+// device-side phase arithmetic and launch wrappers. Not part of the public ABI
+// (include/fpw.h is).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/fpw.h"
+
+namespace fpw {
+
+// Device status bits latched in the context's status word.
+constexpr unsigned kStatusData = 1u;     // sigma <= 0 or non-finite t/x/sigma in some curve
+constexpr unsigned kStatusGrid = 2u;     // non-finite frequency
+constexpr unsigned kStatusTimeout = 4u;  // a bounded wait gave up
+
+// Largest distance (cycles) by which the linear-grid fast path may move a
+// phase relative to frac(t_i * freqs[k]): tiles whose grid deviates more are
+// evaluated with a direct per-frequency anchor instead.
+constexpr double kGridTolCycles = 2e-10;
+
+// One unit of persistent work: frequencies [f_lo, f_hi) of curve `curve`.
+// Its top-k candidates go to row `slot` of the candidate table.
+struct WorkItem {
+  int32_t curve;
+  int32_t f_lo;
+  int32_t f_hi;
+  int32_t slot;
+};
+
+struct TileArgs {
+  const double* t;           // observation times, CSR by curve
+  const int64_t* offsets;    // [ncurves + 1]; NULL: one curve of n_single observations
+  int64_t n_single;
+  const void* aw;            // prep output: float2 or double2 {a = x w, w = 1/sigma^2} per observation
+  const double* freqs;       // [nfreq]
+  int64_t nfreq;
+  const WorkItem* items;     // [nitems], cost-descending
+  int nitems;
+  unsigned* counter;         // work-queue head (zeroed before launch)
+  unsigned* status;          // latched status bits
+  const uint8_t* curve_bad;  // [ncurves] 1 = invalid data
+  double* cand_S;            // [slots * k] candidate peaks (S), or NULL when k == 0
+  int32_t* cand_idx;         // [slots * k]
+  double* S_out;             // dense [ncurves * nfreq] or NULL
+  int M;
+  int k;
+  int peak_raw;
+  int K;                     // FPW_PHASE_FP32 re-anchor interval
+  int obs_chunk;             // observations staged per pass
+  double inv_alpha2;
+};
+
+struct PrepArgs {
+  const double* t;
+  const double* x;
+  const double* sigma;
+  const int64_t* offsets;  // NULL: one curve
+  int64_t ncurves;
+  int64_t nobs;
+  const double* freqs;
+  int64_t nfreq;
+  void* aw;                // float2 or double2 [nobs]
+  int accum64;
+  uint8_t* curve_bad;      // [ncurves], zeroed before launch
+  unsigned* status;
+};
+
+struct MergeArgs {
+  const double* cand_S;
+  const int32_t* cand_idx;
+  const int32_t* cand_base;  // [ncurves + 1] candidate rows per curve
+  const uint8_t* curve_bad;
+  const unsigned* status;
+  int64_t ncurves;
+  int k;
+  int32_t* topk_idx;
+  float* topk_S;
+};
+
+struct PlainArgs {           // binary64 plain form, one curve
+  const double* t;
+  const double* x;
+  const double* sigma;
+  int64_t n;
+  const double* freqs;
+  int64_t nfreq;
+  int M;
+  double inv_alpha2;
+  double* S_out;             // [nfreq]
+  unsigned* status;
+};
+
+struct DenseTopkArgs {       // top-k of one dense periodogram (plain form)
+  const double* S;
+  int64_t nfreq;
+  int k;
+  int peak_raw;
+  int32_t* topk_idx;
+  float* topk_S;
+  const unsigned* status;
+};
+
+struct DebugBinsArgs {
+  const double* t;
+  int64_t n;
+  const double* freqs;
+  int64_t nfreq;
+  int M;
+  int phase_mode;
+  int anchor_every;          // anchor spacing in frequency indices
+  int32_t* bins;             // [nfreq * n]
+};
+
+// Tile-kernel shape chosen by the host (tuned per bin count and curve size).
+struct TileShape {
+  int threads;   // T
+  int R;         // frequencies per thread
+  int obs_chunk; // NC
+  size_t smem;   // dynamic shared memory bytes
+};
+
+// ---- launch wrappers (defined in the .cu files) -------------------------
+size_t tile_smem_bytes(int T, int R, int M, int NC, int k, bool accum64);
+int tile_max_blocks_per_sm(int R, int phase_mode, bool accum64, int T, size_t smem);
+bool tile_supported_R(int R);
+cudaError_t launch_tile(const TileArgs& a, const TileShape& s, int phase_mode, bool accum64, int grid,
+                        cudaStream_t st);
+cudaError_t launch_prep(const PrepArgs& a, cudaStream_t st);
+cudaError_t launch_merge(const MergeArgs& a, cudaStream_t st);
+cudaError_t launch_plain(const PlainArgs& a, cudaStream_t st);
+cudaError_t launch_dense_topk(const DenseTopkArgs& a, cudaStream_t st);
+cudaError_t launch_debug_bins(const DebugBinsArgs& a, cudaStream_t st);
+cudaError_t launch_latch(unsigned* words, cudaStream_t st);  // words[2] |= words[1]
+cudaError_t launch_fill_topk(int32_t* idx, float* S, int64_t n, cudaStream_t st);
+cudaError_t tile_init_attributes(int max_smem);
+cudaError_t plain_init_attributes(int max_smem);
+size_t plain_smem_bytes(int M);
+
+// ---- device arithmetic --------------------------------------------------
+#ifdef __CUDACC__
+
+// v = mant * 2^e2 exactly (mant < 2^53); sign dropped.
+__device__ __forceinline__ void split_binary64(double v, unsigned long long& mant, int& e2) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const int be = (int)((b >> 52) & 0x7ffull);
+  mant = b & 0xFFFFFFFFFFFFFull;
+  if (be == 0) {
+    e2 = -1074;  // zero or subnormal
+  } else {
+    mant |= 1ull << 52;
+    e2 = be - 1075;
+  }
+}
+
+// Phase of t*f as a 64-bit fixed-point fraction of a cycle:
+//   returns floor(frac(t*f) * 2^64) (mod 2^64),
+// computed exactly from the integer product of the two binary64 significands
+// (no binary64 arithmetic: the 106-bit product is formed with integer
+// multiplies and the 64 bits just below the binary point are extracted).
+// For t*f < 0 the result is -floor(|t f| frac) mod 2^64, within one unit
+// (2^-64 cycles) of the exact phase. t and f must be finite.
+__device__ __forceinline__ unsigned long long phase_fixed64(double t, double f) {
+  unsigned long long mt, mf;
+  int et, ef;
+  split_binary64(t, mt, et);
+  split_binary64(f, mf, ef);
+  const unsigned long long lo = mt * mf;
+  const unsigned long long hi = __umul64hi(mt, mf);
+  const int s = et + ef + 64;  // frac * 2^64 = (Q * 2^s) mod 2^64, Q = hi * 2^64 + lo
+  unsigned long long r;
+  if (s >= 64) {
+    r = 0ull;
+  } else if (s >= 0) {
+    r = lo << s;
+  } else {
+    const int sh = -s;
+    if (sh < 64) {
+      r = (lo >> sh) | (hi << (64 - sh));
+    } else if (sh < 128) {
+      r = hi >> (sh - 64);
+    } else {
+      r = 0ull;
+    }
+  }
+  const bool neg = ((__double_as_longlong(t) ^ __double_as_longlong(f)) < 0) && (mt != 0ull) && (mf != 0ull);
+  return neg ? (0ull - r) : r;
+}
+
+// Bin of a 64-bit fixed-point phase: floor(M * Phi_hi / 2^32). It equals
+// floor(M * Phi / 2^64) except within 2^-32 cycles below a bin edge.
+__device__ __forceinline__ unsigned bin_of_phase(unsigned long long phi, unsigned M) {
+  return __umulhi((unsigned)(phi >> 32), M);
+}
+
+// Packed FP32 pair add (one f32x2 instruction on sm_100 and later).
+__device__ __forceinline__ float2 f2add(float2 a, float2 b) {
+  unsigned long long x, y, z;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(x) : "f"(a.x), "f"(a.y));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(y) : "f"(b.x), "f"(b.y));
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(z) : "l"(x), "l"(y));
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(z));
+  return r;
+}
+
+// Ranking used for peaks: larger S first, then lower frequency index.
+__device__ __forceinline__ bool ranks_before(double s1, int k1, double s2, int k2) {
+  return (s1 > s2) || (s1 == s2 && (unsigned)k1 < (unsigned)k2);
+}
+
+#endif  // __CUDACC__
+
+}  // namespace fpw

@@ -1,0 +1,900 @@
+// Host runtime of the GB300 FPW library: the C ABI of include/fpw.h.
+//
+// Responsibilities: argument validation, the per-context device scratch
+// (grow-only buffers), the batch planner (work items over curves and frequency
+// segments, cost-sorted for the persistent kernel), kernel-shape selection,
+// CUDA-graph capture and replay of repeated identical calls, the binary64
+// plain form (one launch per curve), and the host-buffer end-to-end entry.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "fpw_internal.cuh"
+
+using namespace fpw;
+
+namespace {
+
+thread_local char g_last_cuda_error[256] = "";
+
+int cuda_fail(cudaError_t e, const char* what) {
+  snprintf(g_last_cuda_error, sizeof(g_last_cuda_error), "%s: %s", what, cudaGetErrorString(e));
+  if (getenv("FPW_DEBUG")) fprintf(stderr, "[fpw] %s\n", g_last_cuda_error);
+  return e == cudaErrorMemoryAllocation ? FPW_ENOMEM : FPW_ECUDA;
+}
+
+#define FPW_CK(call)                                   \
+  do {                                                 \
+    cudaError_t fpw_e_ = (call);                       \
+    if (fpw_e_ != cudaSuccess) return cuda_fail(fpw_e_, #call); \
+  } while (0)
+
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+};
+
+cudaError_t ensure(DevBuf& b, size_t bytes) {
+  if (bytes <= b.cap && b.p) return cudaSuccess;
+  if (b.p) {
+    cudaError_t e = cudaFree(b.p);  // synchronizes the device
+    b.p = nullptr;
+    b.cap = 0;
+    if (e != cudaSuccess) return e;
+  }
+  size_t want = bytes < 256 ? 256 : bytes;
+  want = (want + 255) & ~(size_t)255;
+  cudaError_t e = cudaMalloc(&b.p, want);
+  if (e != cudaSuccess) {
+    b.p = nullptr;
+    return e;
+  }
+  b.cap = want;
+  return cudaSuccess;
+}
+
+uint64_t fnv1a(const void* data, size_t n, uint64_t h = 1469598103934665603ull) {
+  const unsigned char* p = static_cast<const unsigned char*>(data);
+  for (size_t i = 0; i < n; ++i) {
+    h ^= p[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+template <typename T>
+uint64_t mix(uint64_t h, const T& v) {
+  return fnv1a(&v, sizeof(T), h);
+}
+
+struct Plan {
+  uint64_t key = 0;
+  TileShape shape{};
+  int grid = 0;
+  int nitems = 0;
+  int nslots = 0;
+  DevBuf items, cand_base;
+  uint64_t use = 0;
+};
+
+struct GraphEntry {
+  uint64_t key = 0;
+  cudaGraphExec_t exec = nullptr;
+  uint64_t use = 0;
+};
+
+constexpr int kMaxPlans = 16;
+constexpr int kMaxGraphs = 16;
+
+}  // namespace
+
+struct fpw_ctx {
+  int device = 0;
+  int nsm = 0;
+  int smem_optin = 0;
+  int smem_per_sm = 0;
+  std::mutex mu;
+  cudaStream_t last_stream = nullptr;
+  cudaStream_t own_stream = nullptr;
+  DevBuf aw, cand_S, cand_idx, curve_bad, words, dense;
+  DevBuf h_off, h_t, h_x, h_sigma, h_freqs, h_idx, h_S;  // device copies for the host entry point
+  std::vector<int64_t> off_host;                          // host copy of offsets (when not supplied)
+  std::vector<Plan*> plans;
+  std::vector<GraphEntry> graphs;
+  uint64_t tick = 0;
+  bool timing = false;
+  std::vector<cudaEvent_t> ev;  // pairs (start, stop) of recorded tile launches
+  size_t ev_used = 0;           // events in use (even count)
+};
+
+namespace {
+
+void free_buf(DevBuf& b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.cap = 0;
+}
+
+int status_to_code(unsigned s) {
+  if (s & kStatusTimeout) return FPW_ETIMEOUT;
+  if (s & (kStatusData | kStatusGrid)) return FPW_EDATA;
+  return FPW_OK;
+}
+
+bool valid_params(const fpw_params& p) {
+  if (!(p.inv_alpha2 >= 0.0) || !std::isfinite(p.inv_alpha2)) return false;
+  if (p.phase_mode != FPW_PHASE_FIXED64 && p.phase_mode != FPW_PHASE_FP64 && p.phase_mode != FPW_PHASE_FP32)
+    return false;
+  if (p.accum != FPW_ACCUM_FP32 && p.accum != FPW_ACCUM_FP64) return false;
+  if (p.K < 1) return false;
+  if (p.peak_mode != FPW_PEAK_LOCALMAX && p.peak_mode != FPW_PEAK_RAW) return false;
+  if (p.threads != 0 && (p.threads < 32 || p.threads > 512 || p.threads % 32 != 0)) return false;
+  if (p.freqs_per_thread != 0 && !tile_supported_R(p.freqs_per_thread)) return false;
+  if (p.obs_chunk != 0 && p.obs_chunk < 32) return false;
+  return true;
+}
+
+// Kernel shape: T threads, R frequencies per thread, NC observations per pass.
+// Per-thread bins take R*M*T*(8|16) bytes; the observation chunk takes
+// NC*(16 + 8|16) bytes. Prefer two resident blocks per SM (one stages while the
+// other accumulates); fall back to one when the bins alone do not allow it.
+int choose_shape(fpw_ctx* ctx, const fpw_params& p, int M, int k, int64_t max_n, TileShape& out) {
+  const bool acc64 = p.accum == FPW_ACCUM_FP64;
+  const int T = p.threads ? p.threads : 128;
+  int R = p.freqs_per_thread;
+  if (!R) R = acc64 ? 2 : (M <= 24 ? 4 : 2);
+  const int64_t want_nc = std::max<int64_t>(32, ((max_n + 31) / 32) * 32);
+  const size_t per_sm = (size_t)ctx->smem_per_sm;
+  auto fits = [&](int blocks, int nc) {
+    const size_t s = tile_smem_bytes(T, R, M, nc, k, acc64);
+    return s <= (size_t)ctx->smem_optin && (s + 1024) * blocks <= per_sm;
+  };
+  int NC = p.obs_chunk;
+  if (!NC) {
+    NC = 0;
+    for (int blocks : {2, 1}) {
+      int lo = 32, hi = (int)std::min<int64_t>(want_nc, 1 << 16);
+      if (!fits(blocks, lo)) continue;
+      while (lo < hi) {  // largest multiple of 32 that fits
+        int mid = ((lo + hi + 32) / 64) * 32;
+        if (mid <= lo) mid = lo + 32;
+        if (mid > hi) mid = hi;
+        if (fits(blocks, mid))
+          lo = mid;
+        else
+          hi = mid - 32;
+      }
+      if (blocks == 2 && lo < 256 && lo < want_nc) continue;  // too small a chunk: one block per SM instead
+      NC = lo;
+      break;
+    }
+    if (!NC) return FPW_ENOTSUP;  // the bins alone exceed shared memory
+  }
+  const size_t smem = tile_smem_bytes(T, R, M, NC, k, acc64);
+  if (smem > (size_t)ctx->smem_optin) return FPW_ENOTSUP;
+  out.threads = T;
+  out.R = R;
+  out.obs_chunk = NC;
+  out.smem = smem;
+  return FPW_OK;
+}
+
+// Work items: each curve's frequency range split into segments of whole tiles
+// so that every resident block gets several items (load balance), sorted by
+// cost (observations x frequencies) descending; candidate rows per curve in
+// curve order.
+Plan* build_plan(fpw_ctx* ctx, const int64_t* off, int64_t C, int64_t F, const TileShape& sh, int blocks_per_sm,
+                 uint64_t key, int* err) {
+  *err = FPW_OK;
+  const int64_t Wown = (int64_t)sh.threads * sh.R - 2;
+  const int64_t tiles = (F + Wown - 1) / Wown;
+  const int resident = std::max(1, blocks_per_sm * ctx->nsm);
+  double total = 0.0;
+  for (int64_t c = 0; c < C; ++c) total += (double)(off[c + 1] - off[c] + 32) * (double)F;
+  const double target = std::max(total / (8.0 * resident), 32.0 * (double)Wown * 16.0);
+  std::vector<WorkItem> items;
+  std::vector<double> cost;
+  std::vector<int32_t> base((size_t)C + 1, 0);
+  items.reserve((size_t)C);
+  for (int64_t c = 0; c < C; ++c) {
+    const double cc = (double)(off[c + 1] - off[c] + 32) * (double)F;
+    int64_t nseg = (int64_t)std::llround(cc / target);
+    nseg = std::max<int64_t>(1, std::min<int64_t>(nseg, tiles));
+    base[c + 1] = base[c] + (int32_t)nseg;
+    for (int64_t q = 0; q < nseg; ++q) {
+      const int64_t t0 = tiles * q / nseg, t1 = tiles * (q + 1) / nseg;
+      WorkItem w;
+      w.curve = (int32_t)c;
+      w.f_lo = (int32_t)(t0 * Wown);
+      w.f_hi = (int32_t)std::min<int64_t>(F, t1 * Wown);
+      w.slot = base[c] + (int32_t)q;
+      items.push_back(w);
+      cost.push_back(cc * (double)(t1 - t0) / (double)tiles);
+    }
+  }
+  std::vector<int> order(items.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  std::vector<WorkItem> sorted(items.size());
+  for (size_t i = 0; i < order.size(); ++i) sorted[i] = items[order[i]];
+
+  Plan* pl = new (std::nothrow) Plan();
+  if (!pl) {
+    *err = FPW_ENOMEM;
+    return nullptr;
+  }
+  pl->key = key;
+  pl->shape = sh;
+  pl->nitems = (int)sorted.size();
+  pl->nslots = base[C];
+  pl->grid = std::max(1, std::min(resident, pl->nitems));
+  cudaError_t e = ensure(pl->items, sorted.size() * sizeof(WorkItem));
+  if (e == cudaSuccess) e = ensure(pl->cand_base, base.size() * sizeof(int32_t));
+  if (e == cudaSuccess)
+    e = cudaMemcpy(pl->items.p, sorted.data(), sorted.size() * sizeof(WorkItem), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(pl->cand_base.p, base.data(), base.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    *err = cuda_fail(e, "plan upload");
+    free_buf(pl->items);
+    free_buf(pl->cand_base);
+    delete pl;
+    return nullptr;
+  }
+  return pl;
+}
+
+Plan* get_plan(fpw_ctx* ctx, const int64_t* off, int64_t C, int64_t F, const TileShape& sh, int blocks_per_sm,
+               int* err) {
+  uint64_t key = fnv1a(off, sizeof(int64_t) * (size_t)(C + 1));
+  key = mix(key, C);
+  key = mix(key, F);
+  key = mix(key, sh.threads);
+  key = mix(key, sh.R);
+  key = mix(key, sh.obs_chunk);
+  key = mix(key, sh.smem);
+  key = mix(key, blocks_per_sm);
+  for (Plan* p : ctx->plans)
+    if (p->key == key) {
+      p->use = ++ctx->tick;
+      *err = FPW_OK;
+      return p;
+    }
+  Plan* p = build_plan(ctx, off, C, F, sh, blocks_per_sm, key, err);
+  if (!p) return nullptr;
+  p->use = ++ctx->tick;
+  if ((int)ctx->plans.size() >= kMaxPlans) {
+    auto it = std::min_element(ctx->plans.begin(), ctx->plans.end(),
+                               [](const Plan* a, const Plan* b) { return a->use < b->use; });
+    // graphs may reference the evicted plan's buffers: drop them all
+    for (GraphEntry& g : ctx->graphs) cudaGraphExecDestroy(g.exec);
+    ctx->graphs.clear();
+    free_buf((*it)->items);
+    free_buf((*it)->cand_base);
+    delete *it;
+    ctx->plans.erase(it);
+  }
+  ctx->plans.push_back(p);
+  return p;
+}
+
+int check_offsets(const int64_t* off, int64_t C) {
+  if (off[0] != 0) return FPW_EINVAL;
+  for (int64_t c = 0; c < C; ++c)
+    if (off[c + 1] < off[c]) return FPW_EINVAL;
+  if (off[C] > ((int64_t)1 << 40)) return FPW_EINVAL;
+  return FPW_OK;
+}
+
+struct BatchCall {
+  cudaStream_t stream;
+  fpw_params p;
+  const int64_t* offsets;  // device, or NULL for one curve
+  const int64_t* off_h;    // host offsets [C+1]
+  int64_t C;
+  const double *t, *x, *sigma, *freqs;
+  int64_t F;
+  int M, k;
+  int32_t* topk_idx;
+  float* topk_S;
+  double* S_out;
+};
+
+void drop_graphs(fpw_ctx* ctx) {
+  for (GraphEntry& g : ctx->graphs) cudaGraphExecDestroy(g.exec);
+  ctx->graphs.clear();
+}
+
+// Enqueue prep -> persistent tile kernel -> merge -> status latch.
+int enqueue_tile_path(fpw_ctx* ctx, const BatchCall& b, Plan* pl, unsigned* words) {
+  const bool acc64 = b.p.accum == FPW_ACCUM_FP64;
+  const int64_t nobs = b.off_h[b.C];
+  FPW_CK(cudaMemsetAsync(words, 0, 2 * sizeof(unsigned), b.stream));
+  FPW_CK(cudaMemsetAsync(ctx->curve_bad.p, 0, (size_t)b.C, b.stream));
+  PrepArgs pa{};
+  pa.t = b.t;
+  pa.x = b.x;
+  pa.sigma = b.sigma;
+  pa.offsets = b.offsets;
+  pa.ncurves = b.C;
+  pa.nobs = nobs;
+  pa.freqs = b.freqs;
+  pa.nfreq = b.F;
+  pa.aw = ctx->aw.p;
+  pa.accum64 = acc64 ? 1 : 0;
+  pa.curve_bad = static_cast<uint8_t*>(ctx->curve_bad.p);
+  pa.status = words + 1;
+  FPW_CK(launch_prep(pa, b.stream));
+  TileArgs ta{};
+  ta.t = b.t;
+  ta.offsets = b.offsets;
+  ta.n_single = b.offsets ? 0 : nobs;
+  ta.aw = ctx->aw.p;
+  ta.freqs = b.freqs;
+  ta.nfreq = b.F;
+  ta.items = static_cast<const WorkItem*>(pl->items.p);
+  ta.nitems = pl->nitems;
+  ta.counter = words;
+  ta.status = words + 1;
+  ta.curve_bad = static_cast<const uint8_t*>(ctx->curve_bad.p);
+  ta.cand_S = b.k > 0 ? static_cast<double*>(ctx->cand_S.p) : nullptr;
+  ta.cand_idx = b.k > 0 ? static_cast<int32_t*>(ctx->cand_idx.p) : nullptr;
+  ta.S_out = b.S_out;
+  ta.M = b.M;
+  ta.k = b.k;
+  ta.peak_raw = b.p.peak_mode == FPW_PEAK_RAW ? 1 : 0;
+  ta.K = b.p.K;
+  ta.obs_chunk = pl->shape.obs_chunk;
+  ta.inv_alpha2 = b.p.inv_alpha2;
+  const bool timed = ctx->timing && !b.p.use_graph;
+  if (timed) {
+    while (ctx->ev.size() < ctx->ev_used + 2) {
+      cudaEvent_t e;
+      FPW_CK(cudaEventCreate(&e));
+      ctx->ev.push_back(e);
+    }
+    FPW_CK(cudaEventRecord(ctx->ev[ctx->ev_used], b.stream));
+  }
+  FPW_CK(launch_tile(ta, pl->shape, b.p.phase_mode, acc64, pl->grid, b.stream));
+  if (timed) {
+    FPW_CK(cudaEventRecord(ctx->ev[ctx->ev_used + 1], b.stream));
+    ctx->ev_used += 2;
+  }
+  if (b.k > 0) {
+    MergeArgs ma{};
+    ma.cand_S = static_cast<const double*>(ctx->cand_S.p);
+    ma.cand_idx = static_cast<const int32_t*>(ctx->cand_idx.p);
+    ma.cand_base = static_cast<const int32_t*>(pl->cand_base.p);
+    ma.curve_bad = static_cast<const uint8_t*>(ctx->curve_bad.p);
+    ma.status = words + 1;
+    ma.ncurves = b.C;
+    ma.k = b.k;
+    ma.topk_idx = b.topk_idx;
+    ma.topk_S = b.topk_S;
+    FPW_CK(launch_merge(ma, b.stream));
+  }
+  FPW_CK(launch_latch(words, b.stream));
+  return FPW_OK;
+}
+
+int run_tile_path(fpw_ctx* ctx, const BatchCall& b) {
+  const bool acc64 = b.p.accum == FPW_ACCUM_FP64;
+  int64_t max_n = 0;
+  for (int64_t c = 0; c < b.C; ++c) max_n = std::max(max_n, b.off_h[c + 1] - b.off_h[c]);
+  TileShape sh{};
+  int rc = choose_shape(ctx, b.p, b.M, b.k, max_n, sh);
+  if (rc != FPW_OK) return rc;
+  const int bps = tile_max_blocks_per_sm(sh.R, b.p.phase_mode, acc64, sh.threads, sh.smem);
+  if (bps < 1) return FPW_ENOTSUP;
+  Plan* pl = get_plan(ctx, b.off_h, b.C, b.F, sh, bps, &rc);
+  if (!pl) return rc;
+  const int64_t nobs = b.off_h[b.C];
+  // scratch (grow-only; growing invalidates captured graphs)
+  void* before[5] = {ctx->aw.p, ctx->cand_S.p, ctx->cand_idx.p, ctx->curve_bad.p, ctx->words.p};
+  cudaError_t e = ensure(ctx->aw, (size_t)(nobs + 2) * (acc64 ? 16 : 8));
+  if (e == cudaSuccess && b.k > 0) e = ensure(ctx->cand_S, (size_t)pl->nslots * b.k * sizeof(double));
+  if (e == cudaSuccess && b.k > 0) e = ensure(ctx->cand_idx, (size_t)pl->nslots * b.k * sizeof(int32_t));
+  if (e == cudaSuccess) e = ensure(ctx->curve_bad, (size_t)b.C + 16);
+  if (e != cudaSuccess) return cuda_fail(e, "scratch allocation");
+  void* after[5] = {ctx->aw.p, ctx->cand_S.p, ctx->cand_idx.p, ctx->curve_bad.p, ctx->words.p};
+  if (memcmp(before, after, sizeof(before)) != 0) drop_graphs(ctx);
+  unsigned* words = static_cast<unsigned*>(ctx->words.p);
+
+  if (!b.p.use_graph) return enqueue_tile_path(ctx, b, pl, words);
+
+  uint64_t gk = mix(pl->key, (const void*)b.stream);
+  for (const void* q : {(const void*)b.offsets, (const void*)b.t, (const void*)b.x, (const void*)b.sigma,
+                        (const void*)b.freqs, (const void*)b.topk_idx, (const void*)b.topk_S, (const void*)b.S_out})
+    gk = mix(gk, q);
+  gk = mix(gk, b.C);
+  gk = mix(gk, b.F);
+  gk = mix(gk, b.M);
+  gk = mix(gk, b.k);
+  gk = mix(gk, b.p.inv_alpha2);
+  gk = mix(gk, b.p.phase_mode);
+  gk = mix(gk, b.p.accum);
+  gk = mix(gk, b.p.K);
+  gk = mix(gk, b.p.peak_mode);
+  gk = mix(gk, ctx->aw.p);
+  gk = mix(gk, ctx->cand_S.p);
+  gk = mix(gk, ctx->cand_idx.p);
+  gk = mix(gk, ctx->curve_bad.p);
+  gk = mix(gk, pl);
+  for (GraphEntry& g : ctx->graphs)
+    if (g.key == gk) {
+      g.use = ++ctx->tick;
+      FPW_CK(cudaGraphLaunch(g.exec, b.stream));
+      return FPW_OK;
+    }
+  cudaGraph_t graph = nullptr;
+  FPW_CK(cudaStreamBeginCapture(b.stream, cudaStreamCaptureModeThreadLocal));
+  rc = enqueue_tile_path(ctx, b, pl, words);
+  cudaError_t ec = cudaStreamEndCapture(b.stream, &graph);
+  if (rc != FPW_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (ec != cudaSuccess) return cuda_fail(ec, "cudaStreamEndCapture");
+  cudaGraphExec_t exec = nullptr;
+  ec = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ec != cudaSuccess) return cuda_fail(ec, "cudaGraphInstantiate");
+  if ((int)ctx->graphs.size() >= kMaxGraphs) {
+    auto it = std::min_element(ctx->graphs.begin(), ctx->graphs.end(),
+                               [](const GraphEntry& a, const GraphEntry& b2) { return a.use < b2.use; });
+    cudaGraphExecDestroy(it->exec);
+    ctx->graphs.erase(it);
+  }
+  GraphEntry ge;
+  ge.key = gk;
+  ge.exec = exec;
+  ge.use = ++ctx->tick;
+  ctx->graphs.push_back(ge);
+  FPW_CK(cudaGraphLaunch(exec, b.stream));
+  return FPW_OK;
+}
+
+// The binary64 plain form: per curve one periodogram launch (and one top-k launch).
+int run_plain_path(fpw_ctx* ctx, const BatchCall& b) {
+  unsigned* words = static_cast<unsigned*>(ctx->words.p);
+  FPW_CK(cudaMemsetAsync(words, 0, 2 * sizeof(unsigned), b.stream));
+  // validate frequencies (and observations) once for the status word
+  PrepArgs pa{};
+  pa.t = b.t;
+  pa.x = b.x;
+  pa.sigma = b.sigma;
+  pa.offsets = b.offsets;
+  pa.ncurves = b.C;
+  pa.nobs = b.off_h[b.C];
+  pa.freqs = b.freqs;
+  pa.nfreq = b.F;
+  pa.aw = nullptr;
+  FPW_CK(ensure(ctx->curve_bad, (size_t)b.C + 16));
+  FPW_CK(cudaMemsetAsync(ctx->curve_bad.p, 0, (size_t)b.C, b.stream));
+  pa.curve_bad = static_cast<uint8_t*>(ctx->curve_bad.p);
+  pa.status = words + 1;
+  FPW_CK(launch_prep(pa, b.stream));
+  if (!b.S_out) FPW_CK(ensure(ctx->dense, (size_t)b.F * sizeof(double)));
+  for (int64_t c = 0; c < b.C; ++c) {
+    const int64_t o = b.off_h[c], n = b.off_h[c + 1] - o;
+    double* S = b.S_out ? b.S_out + c * b.F : static_cast<double*>(ctx->dense.p);
+    PlainArgs a{};
+    a.t = b.t + o;
+    a.x = b.x + o;
+    a.sigma = b.sigma + o;
+    a.n = n;
+    a.freqs = b.freqs;
+    a.nfreq = b.F;
+    a.M = b.M;
+    a.inv_alpha2 = b.p.inv_alpha2;
+    a.S_out = S;
+    a.status = words + 1;
+    FPW_CK(launch_plain(a, b.stream));
+    if (b.k > 0) {
+      DenseTopkArgs d{};
+      d.S = S;
+      d.nfreq = b.F;
+      d.k = b.k;
+      d.peak_raw = b.p.peak_mode == FPW_PEAK_RAW ? 1 : 0;
+      d.topk_idx = b.topk_idx + c * b.k;
+      d.topk_S = b.topk_S + c * b.k;
+      FPW_CK(launch_dense_topk(d, b.stream));
+    }
+  }
+  FPW_CK(launch_latch(words, b.stream));
+  return FPW_OK;
+}
+
+int batch_impl(fpw_ctx* ctx, BatchCall& b) {
+  if (b.C == 0) return FPW_OK;
+  if (b.F == 0) {
+    if (b.k > 0) FPW_CK(launch_fill_topk(b.topk_idx, b.topk_S, b.C * b.k, b.stream));
+    return FPW_OK;
+  }
+  if (b.F > ((int64_t)1 << 31) - 1024 || b.C > ((int64_t)1 << 31) - 1) return FPW_EINVAL;
+  if (b.p.phase_mode == FPW_PHASE_FP64) return run_plain_path(ctx, b);
+  return run_tile_path(ctx, b);
+}
+
+int sync_status(fpw_ctx* ctx, cudaStream_t st, int rc) {
+  if (rc != FPW_OK) return rc;
+  FPW_CK(cudaStreamSynchronize(st));
+  unsigned w = 0;
+  FPW_CK(cudaMemcpy(&w, static_cast<unsigned*>(ctx->words.p) + 1, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  return status_to_code(w);
+}
+
+std::mutex g_default_mu;
+fpw_ctx* g_default[64] = {nullptr};
+
+fpw_ctx* default_ctx(int* rc) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    *rc = FPW_ECUDA;
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lk(g_default_mu);
+  if (!g_default[dev]) {
+    *rc = fpw_ctx_create(&g_default[dev], dev);
+    if (*rc != FPW_OK) {
+      g_default[dev] = nullptr;
+      return nullptr;
+    }
+  }
+  *rc = FPW_OK;
+  return g_default[dev];
+}
+
+}  // namespace
+
+extern "C" {
+
+void fpw_params_default(fpw_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->inv_alpha2 = 0.0;
+  p->phase_mode = FPW_PHASE_FIXED64;
+  p->accum = FPW_ACCUM_FP32;
+  p->K = 256;
+  p->peak_mode = FPW_PEAK_LOCALMAX;
+  p->use_graph = 0;
+}
+
+int fpw_version(void) { return 1; }
+
+const char* fpw_strerror(int s) {
+  switch (s) {
+    case FPW_OK: return "ok";
+    case FPW_EINVAL: return "invalid argument";
+    case FPW_EDATA: return "invalid data (sigma <= 0 or a non-finite input)";
+    case FPW_ENOMEM: return "out of memory";
+    case FPW_ECUDA: return "CUDA runtime error";
+    case FPW_ETIMEOUT: return "bounded device wait timed out";
+    case FPW_ENOTSUP: return "unsupported combination of options";
+    default: return "unknown status";
+  }
+}
+
+const char* fpw_last_cuda_error(void) { return g_last_cuda_error; }
+
+int fpw_ctx_create(fpw_ctx** out, int device) {
+  if (!out) return FPW_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return FPW_EINVAL;
+  DeviceGuard g(device);
+  if (!g.ok) return FPW_ECUDA;
+  fpw_ctx* ctx = new (std::nothrow) fpw_ctx();
+  if (!ctx) return FPW_ENOMEM;
+  ctx->device = device;
+  cudaDeviceProp prop;
+  cudaError_t e = cudaGetDeviceProperties(&prop, device);
+  if (e == cudaSuccess) {
+    ctx->nsm = prop.multiProcessorCount;
+    ctx->smem_optin = (int)prop.sharedMemPerBlockOptin;
+    ctx->smem_per_sm = (int)prop.sharedMemPerMultiprocessor;
+    e = tile_init_attributes(ctx->smem_optin);
+  }
+  if (e == cudaSuccess) e = plain_init_attributes(ctx->smem_optin);
+  if (e == cudaSuccess) e = ensure(ctx->words, 64);
+  if (e == cudaSuccess) e = cudaMemset(ctx->words.p, 0, 64);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    int rc = cuda_fail(e, "fpw_ctx_create");
+    free_buf(ctx->words);
+    delete ctx;
+    return rc;
+  }
+  *out = ctx;
+  return FPW_OK;
+}
+
+int fpw_ctx_destroy(fpw_ctx* ctx) {
+  if (!ctx) return FPW_OK;
+  {
+    DeviceGuard g(ctx->device);
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    cudaDeviceSynchronize();
+    drop_graphs(ctx);
+    for (Plan* p : ctx->plans) {
+      free_buf(p->items);
+      free_buf(p->cand_base);
+      delete p;
+    }
+    ctx->plans.clear();
+    for (DevBuf* b : {&ctx->aw, &ctx->cand_S, &ctx->cand_idx, &ctx->curve_bad, &ctx->words, &ctx->dense, &ctx->h_off,
+                      &ctx->h_t, &ctx->h_x, &ctx->h_sigma, &ctx->h_freqs, &ctx->h_idx, &ctx->h_S})
+      free_buf(*b);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
+    for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
+  }
+  delete ctx;
+  return FPW_OK;
+}
+
+int fpw_ctx_set_timing(fpw_ctx* ctx, int enable) {
+  if (!ctx) return FPW_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  ctx->timing = enable != 0;
+  return FPW_OK;
+}
+
+int fpw_ctx_kernel_time(fpw_ctx* ctx, double* ms, int64_t* launches) {
+  if (!ctx || !ms || !launches) return FPW_EINVAL;
+  DeviceGuard g(ctx->device);
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  double total = 0.0;
+  for (size_t i = 0; i + 1 < ctx->ev_used; i += 2) {
+    FPW_CK(cudaEventSynchronize(ctx->ev[i + 1]));
+    float e = 0.f;
+    FPW_CK(cudaEventElapsedTime(&e, ctx->ev[i], ctx->ev[i + 1]));
+    total += e;
+  }
+  *ms = total;
+  *launches = (int64_t)(ctx->ev_used / 2);
+  ctx->ev_used = 0;
+  return FPW_OK;
+}
+
+int fpw_ctx_status(fpw_ctx* ctx) {
+  if (!ctx) return FPW_EINVAL;
+  DeviceGuard g(ctx->device);
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  FPW_CK(cudaStreamSynchronize(ctx->last_stream));
+  unsigned w = 0;
+  FPW_CK(cudaMemcpy(&w, static_cast<unsigned*>(ctx->words.p) + 2, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  FPW_CK(cudaMemset(static_cast<unsigned*>(ctx->words.p) + 2, 0, sizeof(unsigned)));
+  return status_to_code(w);
+}
+
+int fpw_periodogram_batch_ex(fpw_ctx* ctx, void* stream, const fpw_params* params, const int64_t* offsets,
+                             const int64_t* offsets_host, int64_t ncurves, const double* t, const double* x,
+                             const double* sigma, const double* freqs, int64_t nfreq, int M, int k,
+                             int32_t* topk_idx, float* topk_S, double* S_out) {
+  if (!ctx || ncurves < 0 || nfreq < 0 || M < 1 || k < 0 || k > FPW_MAX_TOPK) return FPW_EINVAL;
+  if (ncurves > 0 && !offsets) return FPW_EINVAL;
+  if (ncurves > 0 && nfreq > 0 && !freqs) return FPW_EINVAL;
+  if (ncurves > 0 && k > 0 && (!topk_idx || !topk_S)) return FPW_EINVAL;
+  fpw_params p;
+  fpw_params_default(&p);
+  if (params) p = *params;
+  if (!valid_params(p)) return FPW_EINVAL;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return FPW_ECUDA;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  ctx->last_stream = st;
+  if (ncurves == 0) return FPW_OK;
+  const int64_t* off_h = offsets_host;
+  if (!off_h) {
+    ctx->off_host.resize((size_t)ncurves + 1);
+    FPW_CK(cudaMemcpyAsync(ctx->off_host.data(), offsets, sizeof(int64_t) * (size_t)(ncurves + 1),
+                           cudaMemcpyDeviceToHost, st));
+    FPW_CK(cudaStreamSynchronize(st));
+    off_h = ctx->off_host.data();
+  }
+  if (check_offsets(off_h, ncurves) != FPW_OK) return FPW_EINVAL;
+  if (off_h[ncurves] > 0 && (!t || !x || !sigma)) return FPW_EINVAL;
+  BatchCall b{};
+  b.stream = st;
+  b.p = p;
+  b.offsets = offsets;
+  b.off_h = off_h;
+  b.C = ncurves;
+  b.t = t;
+  b.x = x;
+  b.sigma = sigma;
+  b.freqs = freqs;
+  b.F = nfreq;
+  b.M = M;
+  b.k = k;
+  b.topk_idx = topk_idx;
+  b.topk_S = topk_S;
+  b.S_out = S_out;
+  return batch_impl(ctx, b);
+}
+
+int fpw_periodogram_batch(const int64_t* offsets, int64_t ncurves, const double* t, const double* x,
+                          const double* sigma, const double* freqs, int64_t nfreq, int M, int k, int32_t* topk_idx,
+                          float* topk_S) {
+  int rc = FPW_OK;
+  fpw_ctx* ctx = default_ctx(&rc);
+  if (!ctx) return rc;
+  rc = fpw_periodogram_batch_ex(ctx, nullptr, nullptr, offsets, nullptr, ncurves, t, x, sigma, freqs, nfreq, M, k,
+                                topk_idx, topk_S, nullptr);
+  if (rc != FPW_OK) return rc;
+  DeviceGuard g(ctx->device);
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  return sync_status(ctx, nullptr, rc);
+}
+
+int fpw_periodogram_ex(fpw_ctx* ctx, void* stream, const fpw_params* params, const double* t, const double* x,
+                       const double* sigma, int64_t n, const double* freqs, int64_t nfreq, int M, double* S_out) {
+  if (!ctx || n < 0 || nfreq < 0 || M < 1) return FPW_EINVAL;
+  if (nfreq > 0 && (!freqs || !S_out)) return FPW_EINVAL;
+  if (n > 0 && (!t || !x || !sigma)) return FPW_EINVAL;
+  fpw_params p;
+  fpw_params_default(&p);
+  if (params) p = *params;
+  if (!valid_params(p)) return FPW_EINVAL;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return FPW_ECUDA;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  ctx->last_stream = st;
+  int64_t off_h[2] = {0, n};
+  BatchCall b{};
+  b.stream = st;
+  b.p = p;
+  b.offsets = nullptr;
+  b.off_h = off_h;
+  b.C = 1;
+  b.t = t;
+  b.x = x;
+  b.sigma = sigma;
+  b.freqs = freqs;
+  b.F = nfreq;
+  b.M = M;
+  b.k = 0;
+  b.S_out = S_out;
+  if (nfreq == 0) return FPW_OK;
+  if (p.phase_mode == FPW_PHASE_FP64) {
+    // single curve: the plain kernel reads the curve directly
+    unsigned* words = static_cast<unsigned*>(ctx->words.p);
+    FPW_CK(cudaMemsetAsync(words, 0, 2 * sizeof(unsigned), st));
+    FPW_CK(ensure(ctx->curve_bad, 16));
+    PrepArgs pa{};
+    pa.t = t;
+    pa.x = x;
+    pa.sigma = sigma;
+    pa.ncurves = 1;
+    pa.nobs = n;
+    pa.freqs = freqs;
+    pa.nfreq = nfreq;
+    pa.curve_bad = static_cast<uint8_t*>(ctx->curve_bad.p);
+    pa.status = words + 1;
+    FPW_CK(launch_prep(pa, st));
+    PlainArgs a{};
+    a.t = t;
+    a.x = x;
+    a.sigma = sigma;
+    a.n = n;
+    a.freqs = freqs;
+    a.nfreq = nfreq;
+    a.M = M;
+    a.inv_alpha2 = p.inv_alpha2;
+    a.S_out = S_out;
+    a.status = words + 1;
+    FPW_CK(launch_plain(a, st));
+    FPW_CK(launch_latch(words, st));
+    return FPW_OK;
+  }
+  return batch_impl(ctx, b);
+}
+
+int fpw_periodogram(const double* t, const double* x, const double* sigma, int64_t n, const double* freqs,
+                    int64_t nfreq, int M, double* S_out) {
+  int rc = FPW_OK;
+  fpw_ctx* ctx = default_ctx(&rc);
+  if (!ctx) return rc;
+  rc = fpw_periodogram_ex(ctx, nullptr, nullptr, t, x, sigma, n, freqs, nfreq, M, S_out);
+  if (rc != FPW_OK) return rc;
+  DeviceGuard g(ctx->device);
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  return sync_status(ctx, nullptr, rc);
+}
+
+int fpw_periodogram_batch_host(fpw_ctx* ctx, const fpw_params* params, const int64_t* offsets, int64_t ncurves,
+                               const double* t, const double* x, const double* sigma, const double* freqs,
+                               int64_t nfreq, int M, int k, int32_t* topk_idx, float* topk_S) {
+  if (!ctx || ncurves < 0 || nfreq < 0 || M < 1 || k < 0 || k > FPW_MAX_TOPK) return FPW_EINVAL;
+  if (ncurves == 0) return FPW_OK;
+  if (!offsets || (nfreq > 0 && !freqs) || (k > 0 && (!topk_idx || !topk_S))) return FPW_EINVAL;
+  if (check_offsets(offsets, ncurves) != FPW_OK) return FPW_EINVAL;
+  const int64_t nobs = offsets[ncurves];
+  if (nobs > 0 && (!t || !x || !sigma)) return FPW_EINVAL;
+  cudaStream_t st = nullptr;
+  {
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return FPW_ECUDA;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    st = ctx->own_stream;
+    FPW_CK(ensure(ctx->h_off, sizeof(int64_t) * (size_t)(ncurves + 1)));
+    FPW_CK(ensure(ctx->h_t, sizeof(double) * (size_t)std::max<int64_t>(nobs, 1)));
+    FPW_CK(ensure(ctx->h_x, sizeof(double) * (size_t)std::max<int64_t>(nobs, 1)));
+    FPW_CK(ensure(ctx->h_sigma, sizeof(double) * (size_t)std::max<int64_t>(nobs, 1)));
+    FPW_CK(ensure(ctx->h_freqs, sizeof(double) * (size_t)std::max<int64_t>(nfreq, 1)));
+    FPW_CK(ensure(ctx->h_idx, sizeof(int32_t) * (size_t)std::max<int64_t>(ncurves * k, 1)));
+    FPW_CK(ensure(ctx->h_S, sizeof(float) * (size_t)std::max<int64_t>(ncurves * k, 1)));
+    FPW_CK(cudaMemcpyAsync(ctx->h_off.p, offsets, sizeof(int64_t) * (size_t)(ncurves + 1), cudaMemcpyHostToDevice, st));
+    if (nobs > 0) {
+      FPW_CK(cudaMemcpyAsync(ctx->h_t.p, t, sizeof(double) * (size_t)nobs, cudaMemcpyHostToDevice, st));
+      FPW_CK(cudaMemcpyAsync(ctx->h_x.p, x, sizeof(double) * (size_t)nobs, cudaMemcpyHostToDevice, st));
+      FPW_CK(cudaMemcpyAsync(ctx->h_sigma.p, sigma, sizeof(double) * (size_t)nobs, cudaMemcpyHostToDevice, st));
+    }
+    if (nfreq > 0)
+      FPW_CK(cudaMemcpyAsync(ctx->h_freqs.p, freqs, sizeof(double) * (size_t)nfreq, cudaMemcpyHostToDevice, st));
+  }
+  int rc = fpw_periodogram_batch_ex(ctx, st, params, static_cast<const int64_t*>(ctx->h_off.p), offsets, ncurves,
+                                    static_cast<const double*>(ctx->h_t.p), static_cast<const double*>(ctx->h_x.p),
+                                    static_cast<const double*>(ctx->h_sigma.p),
+                                    static_cast<const double*>(ctx->h_freqs.p), nfreq, M, k,
+                                    static_cast<int32_t*>(ctx->h_idx.p), static_cast<float*>(ctx->h_S.p), nullptr);
+  DeviceGuard g(ctx->device);
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (rc != FPW_OK) {
+    cudaStreamSynchronize(st);
+    return rc;
+  }
+  if (k > 0) {
+    FPW_CK(cudaMemcpyAsync(topk_idx, ctx->h_idx.p, sizeof(int32_t) * (size_t)(ncurves * k), cudaMemcpyDeviceToHost, st));
+    FPW_CK(cudaMemcpyAsync(topk_S, ctx->h_S.p, sizeof(float) * (size_t)(ncurves * k), cudaMemcpyDeviceToHost, st));
+  }
+  return sync_status(ctx, st, FPW_OK);
+}
+
+int fpw_debug_bins(fpw_ctx* ctx, void* stream, const fpw_params* params, const double* t, int64_t n,
+                   const double* freqs, int64_t nfreq, int M, int32_t* bins_out) {
+  if (!ctx || n < 0 || nfreq < 0 || M < 1) return FPW_EINVAL;
+  if (n > 0 && nfreq > 0 && (!t || !freqs || !bins_out)) return FPW_EINVAL;
+  fpw_params p;
+  fpw_params_default(&p);
+  if (params) p = *params;
+  if (!valid_params(p)) return FPW_EINVAL;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return FPW_ECUDA;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  ctx->last_stream = st;
+  DebugBinsArgs a{};
+  a.t = t;
+  a.n = n;
+  a.freqs = freqs;
+  a.nfreq = nfreq;
+  a.M = M;
+  a.phase_mode = p.phase_mode;
+  a.anchor_every = p.phase_mode == FPW_PHASE_FP32 ? p.K : 512;
+  a.bins = bins_out;
+  FPW_CK(launch_debug_bins(a, st));
+  return FPW_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,285 @@
+"""GPU parity: the sm_103a kernels (through the C ABI) against the FP64 oracle on
+the same seeded inputs."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import lightcurves as L
+import oracle
+from gpu_util import assert_S_close, check_topk, run_batch, run_single, s_bound, to_dev
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+G = None
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    global G
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2502_00243_gb300 as G_
+    G = G_
+    c = G.Context(0)
+    yield c
+    c.close()
+
+
+def P(**kw):
+    return G.fpw_params_default(**kw)
+
+
+# ------------------------------------------------------------------ single curve, plain sinusoid (10^4 freqs)
+def test_single_plain_dense_default(ctx):
+    w = L.make("single_plain")
+    t, x, s = w.curve(0)
+    S_or = oracle.fpw(t, x, s, w.freqs, w.M)
+    S_g, st = run_single(ctx, t, x, s, w.freqs, w.M)
+    assert st == 0
+    assert_S_close(S_g, S_or, s_bound(x, s), what="single_plain fixed64/fp32")
+
+
+def test_single_plain_fp64_plain_form_matches_bitwise(ctx):
+    w = L.make("single_plain")
+    t, x, s = w.curve(0)
+    for c in (0.0, 1.0):
+        S_or = oracle.fpw(t, x, s, w.freqs, w.M, c)
+        S_g, st = run_single(ctx, t, x, s, w.freqs, w.M, P(phase_mode=G.FPW_PHASE_FP64, inv_alpha2=c))
+        assert st == 0
+        # same binary64 operations in the same order: identical bins and sums
+        np.testing.assert_array_equal(S_g, S_or)
+
+
+def test_single_plain_fixed64_fp64_sums(ctx):
+    w = L.make("single_plain")
+    t, x, s = w.curve(0)
+    S_or = oracle.fpw(t, x, s, w.freqs, w.M, 0.3)
+    S_g, st = run_single(ctx, t, x, s, w.freqs, w.M, P(accum=G.FPW_ACCUM_FP64, inv_alpha2=0.3))
+    assert st == 0
+    assert_S_close(S_g, S_or, s_bound(x, s), rel=1e-6, absf=1e-9, what="fixed64/fp64 sums")
+
+
+# ------------------------------------------------------------------ single ZTF-like curve, 10^6 freqs
+def test_single_ztf_full_grid(ctx):
+    w = L.make("single_ztf")
+    t, x, s = w.curve(0)
+    S_or = oracle.fpw_parallel(t, x, s, w.freqs, w.M)
+    near = oracle.min_edge_parallel(t, w.freqs, w.M) <= 1e-9
+    S_g, st = run_single(ctx, t, x, s, w.freqs, w.M)
+    assert st == 0
+    assert_S_close(S_g, S_or, s_bound(x, s), mask=~near, what="single_ztf dense")
+    # top-5 through the batch path on the same curve
+    idx, Sk, _, st = run_batch(ctx, w)
+    assert st == 0
+    o_idx, o_S = oracle.topk(S_or, 12)
+    check_topk(idx[0], Sk[0], o_idx, o_S, o_dense=S_or, abs_tol=1e-7 * s_bound(x, s), what="single_ztf topk")
+
+
+# ------------------------------------------------------------------ ragged batches, edge sizes
+RAGGED = [
+    # (ns, nfreq, M, k, params)
+    ([0, 1, 2, 31, 32, 33, 127, 500], 1021, 20, 5, {}),
+    ([3000, 1, 1025, 64], 3001, 10, 8, {"obs_chunk": 256}),
+    ([700, 0, 250], 1, 5, 3, {}),
+    ([700, 250, 40], 2, 5, 3, {}),
+    ([400, 900], 509, 50, 64, {}),
+    ([400, 900], 510, 50, 5, {"freqs_per_thread": 8, "threads": 64}),
+    ([333, 1200], 2048, 1, 4, {}),
+    ([333, 1200, 77], 4097, 3, 6, {"freqs_per_thread": 2, "threads": 256}),
+    ([1500, 10, 800], 2500, 20, 5, {"accum": 1}),
+    ([1500, 10, 800], 2500, 20, 5, {"peak_mode": 1}),
+    ([600, 2100], 1999, 64, 7, {"inv_alpha2": 0.5}),
+]
+
+
+@pytest.mark.parametrize("case", range(len(RAGGED)))
+def test_ragged_batches_dense_and_topk(ctx, case):
+    ns, F, M, k, kw = RAGGED[case]
+    w = L.ragged(case, ns, F, M=M, k=k)
+    p = P(**kw)
+    c = kw.get("inv_alpha2", 0.0)
+    raw = kw.get("peak_mode", 0) == 1
+    idx, Sk, Sd, st = run_batch(ctx, w, params=p, dense=True)
+    assert st == 0
+    S_or, o_idx, o_S = oracle.fpw_batch(w.offsets, w.t, w.x, w.sigma, w.freqs, M, c, k=k + 4, raw=raw)
+    rel = 1e-6 if kw.get("accum", 0) == 1 else 1e-4
+    for ci in range(w.ncurves):
+        t, x, s = w.curve(ci)
+        near = oracle.min_edge(t, w.freqs, M) <= 1e-9 if t.size else np.zeros(F, bool)
+        bound = s_bound(x, s)
+        assert_S_close(Sd[ci], S_or[ci], bound, rel=rel, mask=~near, what=f"case {case} curve {ci} dense")
+        check_topk(idx[ci], Sk[ci], o_idx[ci], o_S[ci], rel=rel, abs_tol=1e-7 * bound, o_dense=S_or[ci],
+                   what=f"case {case} curve {ci}")
+
+
+def test_empty_curve_peaks(ctx):
+    w = L.ragged(50, [0, 10], 100, M=4, k=3)
+    idx, Sk, Sd, st = run_batch(ctx, w, dense=True)
+    assert st == 0
+    assert np.all(Sd[0] == 0.0)
+    # a flat zero periodogram has exactly one peak, at frequency 0
+    assert list(idx[0]) == [0, -1, -1] and Sk[0][0] == 0.0 and np.isnan(Sk[0][1:]).all()
+
+
+# ------------------------------------------------------------------ bins: t*f up to 10^6 cycles
+def _bins_case(ctx, mode, K=256, M=20, nfreq=3000, f_start=499.0):
+    rng = np.random.default_rng(5)
+    t = np.sort(rng.uniform(0, 2000, 300))
+    full = L.freq_grid("precision")
+    a = int(np.searchsorted(full, f_start))
+    freqs = full[a:a + nfreq]
+    tt = torch.from_numpy(t).cuda()
+    ff = torch.from_numpy(freqs).cuda()
+    out = torch.empty(nfreq * t.size, dtype=torch.int32, device="cuda")
+    G.fpw_debug_bins(ctx, None, P(phase_mode=mode, K=K), tt, ff, M, out)
+    torch.cuda.synchronize()
+    b_or, e_or = oracle.bins(t, freqs, M)
+    return out.cpu().numpy().reshape(nfreq, t.size), b_or, e_or
+
+
+def test_bins_fixed64_identical_off_edge(ctx):
+    g, b, e = _bins_case(ctx, G.FPW_PHASE_FIXED64)
+    mism = g != b
+    assert np.all(e[mism] <= 1e-9), f"{int((mism & (e > 1e-9)).sum())} mismatches beyond 1e-9 cycles"
+    assert np.all((g >= 0) & (g < 20))
+
+
+def test_bins_fp64_plain_identical(ctx):
+    g, b, e = _bins_case(ctx, G.FPW_PHASE_FP64)
+    np.testing.assert_array_equal(g, b)
+
+
+@pytest.mark.parametrize("K", [64, 256, 1024])
+def test_bins_fp32_phase_mismatch_within_analytic_margin(ctx, K):
+    g, b, e = _bins_case(ctx, G.FPW_PHASE_FP32, K=K)
+    mism = g != b
+    margin = (2 * K + 4) * 2.0 ** -24
+    assert np.all(e[mism] <= margin), f"K={K}: mismatch at edge distance {e[mism].max()} > {margin}"
+    print(f"fp32 phase K={K}: mismatch rate {mism.mean():.3e}")
+
+
+# ------------------------------------------------------------------ non-linear grid
+def test_nonlinear_grid_uses_direct_anchor(ctx):
+    w = L.ragged(77, [900, 300], 10)
+    rng = np.random.default_rng(1)
+    freqs = np.sort(rng.uniform(0.01, 30.0, 1500))
+    t, x, s = w.curve(0)
+    S_or = oracle.fpw(t, x, s, freqs, 12)
+    S_g, st = run_single(ctx, t, x, s, freqs, 12)
+    assert st == 0
+    near = oracle.min_edge(t, freqs, 12) <= 1e-9
+    assert_S_close(S_g, S_or, s_bound(x, s), mask=~near, what="non-linear grid")
+
+
+# ------------------------------------------------------------------ errors
+def test_invalid_data_reported_per_curve(ctx):
+    w = L.ragged(9, [100, 200, 300], 500, M=10, k=3)
+    sig = w.sigma.copy()
+    sig[150] = 0.0  # curve 1
+    w.sigma = sig
+    idx, Sk, Sd, st = run_batch(ctx, w, dense=True)
+    assert st == G.FPW_EDATA
+    assert np.all(idx[1] == -1) and np.isnan(Sk[1]).all() and np.isnan(Sd[1]).all()
+    S_or, o_idx, o_S = oracle.fpw_batch(w.offsets[:2], w.t, w.x, w.sigma, w.freqs, 10, k=6)
+    check_topk(idx[0], Sk[0], o_idx[0], o_S[0], o_dense=S_or[0], what="valid curve next to a bad one")
+    assert ctx.status() == 0  # cleared by the previous read
+
+
+def test_invalid_frequency_and_sync_entry_points(ctx):
+    w = L.ragged(10, [50], 64, M=4, k=2)
+    d = to_dev(w)
+    d["freqs"][3] = float("nan")
+    S = torch.empty(64, dtype=torch.float64, device="cuda")
+    with pytest.raises(G.FPWError) as ei:
+        G.fpw_periodogram(d["t"], d["x"], d["sigma"], d["freqs"], 4, S)
+    assert ei.value.code == G.FPW_EDATA
+    d["freqs"][3] = 1.0
+    sig = d["sigma"].clone()
+    sig[0] = -1.0
+    with pytest.raises(G.FPWError) as ei:
+        G.fpw_periodogram(d["t"], d["x"], sig, d["freqs"], 4, S)
+    assert ei.value.code == G.FPW_EDATA
+    G.fpw_periodogram(d["t"], d["x"], d["sigma"], d["freqs"], 4, S)  # recovers
+
+
+def test_invalid_arguments_rejected_before_launch(ctx):
+    w = L.ragged(11, [20, 30], 16, M=4, k=2)
+    d = to_dev(w)
+    idx = torch.empty(4, dtype=torch.int32, device="cuda")
+    S = torch.empty(4, dtype=torch.float32, device="cuda")
+    for M, k in ((0, 2), (4, -1), (4, G.FPW_MAX_TOPK + 1)):
+        with pytest.raises(G.FPWError) as ei:
+            G.fpw_periodogram_batch_ex(ctx, None, None, d["offsets"], w.offsets, d["t"], d["x"], d["sigma"],
+                                       d["freqs"], M, k, idx, S)
+        assert ei.value.code == G.FPW_EINVAL
+    bad_off = np.array([0, 30, 20], dtype=np.int64)
+    with pytest.raises(G.FPWError) as ei:
+        G.fpw_periodogram_batch_ex(ctx, None, None, d["offsets"], bad_off, d["t"], d["x"], d["sigma"], d["freqs"], 4,
+                                   2, idx, S)
+    assert ei.value.code == G.FPW_EINVAL
+    for bad in (P(K=0), P(threads=48), P(freqs_per_thread=3), P(inv_alpha2=-1.0), P(phase_mode=9)):
+        with pytest.raises(G.FPWError) as ei:
+            G.fpw_periodogram_batch_ex(ctx, None, bad, d["offsets"], w.offsets, d["t"], d["x"], d["sigma"],
+                                       d["freqs"], 4, 2, idx, S)
+        assert ei.value.code == G.FPW_EINVAL
+
+
+# ------------------------------------------------------------------ graphs, host entry point, plain batch
+def test_graph_replay_matches_direct(ctx):
+    w = L.ragged(12, [300, 1000, 20, 2000], 5000, M=20, k=5)
+    d = to_dev(w)
+    a = run_batch(ctx, w, d=d)
+    g1 = run_batch(ctx, w, d=d, params=P(use_graph=1))
+    g2 = run_batch(ctx, w, d=d, params=P(use_graph=1))
+    for r in (g1, g2):
+        np.testing.assert_array_equal(r[0], a[0])
+        np.testing.assert_array_equal(r[1], a[1])
+
+
+def test_host_entry_point_matches_device_call(ctx):
+    w = L.ragged(13, [300, 1000, 20], 3000, M=10, k=4)
+    a = run_batch(ctx, w)
+    idx = np.empty(w.ncurves * 4, dtype=np.int32)
+    S = np.empty(w.ncurves * 4, dtype=np.float32)
+    G.fpw_periodogram_batch_host(ctx, None, w.offsets, w.t, w.x, w.sigma, w.freqs, 10, 4, idx, S)
+    np.testing.assert_array_equal(idx.reshape(-1, 4), a[0])
+    np.testing.assert_array_equal(S.reshape(-1, 4), a[1])
+
+
+def test_plain_fp64_batch_form(ctx):
+    w = L.ragged(14, [300, 0, 800, 50], 2000, M=20, k=5)
+    idx, Sk, Sd, st = run_batch(ctx, w, dense=True, params=P(phase_mode=G.FPW_PHASE_FP64))
+    assert st == 0
+    S_or, o_idx, o_S = oracle.fpw_batch(w.offsets, w.t, w.x, w.sigma, w.freqs, 20, k=5)
+    np.testing.assert_array_equal(Sd, S_or)
+    for ci in range(w.ncurves):
+        np.testing.assert_array_equal(idx[ci], o_idx[ci])
+        np.testing.assert_array_equal(Sk[ci], o_S[ci].astype(np.float32))
+
+
+# ------------------------------------------------------------------ full-size workloads, sampled outputs
+def test_ragged_10k_full_size_sampled(ctx):
+    w = L.make("ragged_10k")
+    idx, Sk, _, st = run_batch(ctx, w)
+    assert st == 0
+    sample = np.random.default_rng(3).choice(w.ncurves, 12, replace=False)
+    sub = L.make("ragged_10k", sample)
+    _, o_idx, o_S = oracle.fpw_batch(sub.offsets, sub.t, sub.x, sub.sigma, sub.freqs, sub.M, dense=False, k=9)
+    for j, ci in enumerate(sample):
+        t, x, s = sub.curve(j)
+        check_topk(idx[ci], Sk[ci], o_idx[j], o_S[j], abs_tol=1e-7 * s_bound(x, s), what=f"ragged_10k curve {ci}")
+
+
+def test_sweep_batch_full_size_sampled(ctx):
+    """One 10^4-curve batch of the 10^5-curve sweep, as the benchmark launches it."""
+    w = L.make("sweep_100k", range(10_000))
+    idx, Sk, _, st = run_batch(ctx, w)
+    assert st == 0
+    sample = np.random.default_rng(4).choice(w.ncurves, 8, replace=False)
+    sub = L.make("sweep_100k", sample)
+    _, o_idx, o_S = oracle.fpw_batch(sub.offsets, sub.t, sub.x, sub.sigma, sub.freqs, sub.M, dense=False, k=9)
+    for j, ci in enumerate(sample):
+        t, x, s = sub.curve(j)
+        check_topk(idx[ci], Sk[ci], o_idx[j], o_S[j], abs_tol=1e-7 * s_bound(x, s), what=f"sweep curve {ci}")

@@ -31,8 +31,8 @@ MUTATIONS = {
     "peak_left_nonstrict": ("return S[k] > S[k - 1] && S[k] >= S[k + 1];", "return S[k] >= S[k - 1] && S[k] >= S[k + 1];"),
     "tie_to_higher_index": ("return k1 < k2;", "return k1 > k2;"),
     "ends_never_peaks": ("if (k == 0) return S[0] >= S[1];", "if (k == 0) return 0;"),
-    "edge_distance_drops_product_error": ("double d = fabs(r + (ue + (double)M * e)) / (double)M;",
-                                          "double d = fabs(r + ue) / (double)M;"),
+    "edge_distance_drops_product_error": ("return fabs(r + (ue + (double)M * e)) / (double)M;",
+                                          "return fabs(r + ue) / (double)M;"),
 }
 
 
