@@ -170,11 +170,16 @@ def sm_max_mhz():
         return SM_MAX_MHZ_NOMINAL
 
 
+def grid(args):
+    import numpy as np
+    return np.linspace(0.01, 50.0, args.nfreq, dtype=np.float64)
+
+
 def config_block(args, nbatches, batch_evals_mean):
     return {"workload": f"{WORKLOAD}: 1e5 ZTF-like curves, N log-uniform 100-3000, mixed waveforms, M={args.M}, "
-                        f"5e5 linear freqs 0.01-50 1/d, top-{args.k}; one step = one batch of {args.batch_curves} "
+                        f"{args.nfreq:.0e} linear freqs 0.01-50 1/d, top-{args.k}; one step = one batch of {args.batch_curves} "
                         f"curves ({nbatches} batches)",
-            "curves_per_step": args.batch_curves, "nfreq": 500_000, "M": args.M, "k": args.k,
+            "curves_per_step": args.batch_curves, "nfreq": args.nfreq, "M": args.M, "k": args.k,
             "phase": "fixed64 (exact integer anchor + 64-bit stepping)", "bin_sums": "f32",
             "evals_per_step_mean": batch_evals_mean,
             "l2": "inputs larger than L2 (>= 200 MB of float64 per batch, distinct batch each step)"}
@@ -218,7 +223,7 @@ def run_reference(args):
     steps = args.warmup + args.steps
     ids = sorted({s % nb for s in range(steps)})
     batches = make_batches(ids, args.batch_curves, args.M, workers=min(cores, 16))
-    F_grid = L.freq_grid(WORKLOAD)
+    F_grid = grid(args)
     _, F_s = oracle_sample(batches[ids[0]], F_grid, args.M, args.k, args.ref_step_seconds, cores)
     total_ev, total_t = 0.0, 0.0
     for s in range(steps):
@@ -268,7 +273,7 @@ def run_gb300(args):
     t_gen = time.perf_counter()
     host = make_batches(ids, args.batch_curves, args.M, workers=workers)
     t_gen = time.perf_counter() - t_gen
-    F_grid = L.freq_grid(WORKLOAD)
+    F_grid = grid(args)
     F = F_grid.shape[0]
     dev = {b: dict(offsets=torch.from_numpy(h[0]).cuda(), t=torch.from_numpy(h[1]).cuda(),
                    x=torch.from_numpy(h[2]).cuda(), sigma=torch.from_numpy(h[3]).cuda()) for b, h in host.items()}
@@ -441,6 +446,8 @@ def main(argv=None):
     ap.add_argument("--k", type=int, default=5)
     ap.add_argument("--batch-curves", type=int, default=10_000)
     ap.add_argument("--curves-total", type=int, default=100_000)
+    ap.add_argument("--nfreq", type=int, default=500_000,
+                    help="linear grid points over 0.01-50 1/d (the sweep uses 5e5; fewer for small profiling runs)")
     ap.add_argument("--plain-curves", type=int, default=32)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-step-seconds", type=float, default=3.0)

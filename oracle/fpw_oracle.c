@@ -290,18 +290,18 @@ int oracle_bins(const double* t, int64_t n, const double* freqs, int64_t nfreq, 
   return ORACLE_OK;
 }
 
-/* Per frequency: the smallest NONZERO exact edge distance over all
- * observations. A frequency whose value is tiny has an observation whose bin is
- * decided by rounding. Observations exactly on an edge (distance 0, e.g. t = 0)
- * are skipped: there frac(t f) is a short dyadic fraction that every exact
- * method, and binary64 for |t f| < 2^50, assigns to the upper bin. */
+/* Per frequency: the smallest exact edge distance over all observations with
+ * t*f != 0. A frequency whose value is tiny has an observation whose bin is
+ * decided by rounding. Observations with t*f == 0 (t = 0 or f = 0) have phase
+ * exactly 0 in every arithmetic and are skipped. */
 int oracle_min_edge(const double* t, int64_t n, const double* freqs, int64_t nfreq, int M, double* out) {
   if (n < 0 || nfreq < 0 || M < 1 || (nfreq > 0 && !out)) return ORACLE_EINVAL;
   for (int64_t k = 0; k < nfreq; ++k) {
     double best = INFINITY;
     for (int64_t i = 0; i < n; ++i) {
+      if (t[i] == 0.0 || freqs[k] == 0.0) continue;
       double d = edge_distance(t[i], freqs[k], M);
-      if (d > 0.0 && d < best) best = d;
+      if (d < best) best = d;
     }
     out[k] = best;
   }

@@ -153,13 +153,16 @@ __device__ __forceinline__ void split_binary64(double v, unsigned long long& man
   }
 }
 
-// Phase of t*f as a 64-bit fixed-point fraction of a cycle:
-//   returns floor(frac(t*f) * 2^64) (mod 2^64),
+// Phase of t*f as a 64-bit fixed-point fraction of a cycle, rounded UP:
+//   returns ceil(frac(t*f) * 2^64) (mod 2^64),
 // computed exactly from the integer product of the two binary64 significands
 // (no binary64 arithmetic: the 106-bit product is formed with integer
 // multiplies and the 64 bits just below the binary point are extracted).
-// For t*f < 0 the result is -floor(|t f| frac) mod 2^64, within one unit
-// (2^-64 cycles) of the exact phase. t and f must be finite.
+// Rounding up makes every anchor and step an upper bound of the exact value,
+// so a phase stepped from them never falls below the exact phase: a phase
+// exactly on a bin edge stays in the upper bin (bins are half-open), as in
+// exact arithmetic. For t*f < 0 the result is -floor(frac(|t f|) 2^64) mod 2^64,
+// also an upper bound. t and f must be finite.
 __device__ __forceinline__ unsigned long long phase_fixed64(double t, double f) {
   unsigned long long mt, mf;
   int et, ef;
@@ -169,22 +172,28 @@ __device__ __forceinline__ unsigned long long phase_fixed64(double t, double f) 
   const unsigned long long hi = __umul64hi(mt, mf);
   const int s = et + ef + 64;  // frac * 2^64 = (Q * 2^s) mod 2^64, Q = hi * 2^64 + lo
   unsigned long long r;
+  bool inexact;
   if (s >= 64) {
     r = 0ull;
+    inexact = false;
   } else if (s >= 0) {
     r = lo << s;
+    inexact = false;
   } else {
     const int sh = -s;
     if (sh < 64) {
       r = (lo >> sh) | (hi << (64 - sh));
+      inexact = (lo << (64 - sh)) != 0ull;
     } else if (sh < 128) {
       r = hi >> (sh - 64);
+      inexact = lo != 0ull || (sh > 64 && (hi << (128 - sh)) != 0ull);
     } else {
       r = 0ull;
+      inexact = (lo | hi) != 0ull;
     }
   }
   const bool neg = ((__double_as_longlong(t) ^ __double_as_longlong(f)) < 0) && (mt != 0ull) && (mf != 0ull);
-  return neg ? (0ull - r) : r;
+  return neg ? (0ull - r) : (r + (inexact ? 1ull : 0ull));
 }
 
 // Bin of a 64-bit fixed-point phase: floor(M * Phi_hi / 2^32). It equals

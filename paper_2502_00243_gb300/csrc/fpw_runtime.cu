@@ -133,6 +133,10 @@ void free_buf(DevBuf& b) {
   b.cap = 0;
 }
 
+// Discard a stale error left by an earlier, unrelated runtime call so that the
+// launch checks below report only this call's errors.
+void clear_stale_error() { (void)cudaGetLastError(); }
+
 int status_to_code(unsigned s) {
   if (s & kStatusTimeout) return FPW_ETIMEOUT;
   if (s & (kStatusData | kStatusGrid)) return FPW_EDATA;
@@ -324,11 +328,11 @@ void drop_graphs(fpw_ctx* ctx) {
 }
 
 // Enqueue prep -> persistent tile kernel -> merge -> status latch.
-int enqueue_tile_path(fpw_ctx* ctx, const BatchCall& b, Plan* pl, unsigned* words) {
+int enqueue_tile_path(fpw_ctx* ctx, const BatchCall& b, Plan* pl, unsigned* words, cudaStream_t st) {
   const bool acc64 = b.p.accum == FPW_ACCUM_FP64;
   const int64_t nobs = b.off_h[b.C];
-  FPW_CK(cudaMemsetAsync(words, 0, 2 * sizeof(unsigned), b.stream));
-  FPW_CK(cudaMemsetAsync(ctx->curve_bad.p, 0, (size_t)b.C, b.stream));
+  FPW_CK(cudaMemsetAsync(words, 0, 2 * sizeof(unsigned), st));
+  FPW_CK(cudaMemsetAsync(ctx->curve_bad.p, 0, (size_t)b.C, st));
   PrepArgs pa{};
   pa.t = b.t;
   pa.x = b.x;
@@ -342,7 +346,7 @@ int enqueue_tile_path(fpw_ctx* ctx, const BatchCall& b, Plan* pl, unsigned* word
   pa.accum64 = acc64 ? 1 : 0;
   pa.curve_bad = static_cast<uint8_t*>(ctx->curve_bad.p);
   pa.status = words + 1;
-  FPW_CK(launch_prep(pa, b.stream));
+  FPW_CK(launch_prep(pa, st));
   TileArgs ta{};
   ta.t = b.t;
   ta.offsets = b.offsets;
@@ -371,11 +375,11 @@ int enqueue_tile_path(fpw_ctx* ctx, const BatchCall& b, Plan* pl, unsigned* word
       FPW_CK(cudaEventCreate(&e));
       ctx->ev.push_back(e);
     }
-    FPW_CK(cudaEventRecord(ctx->ev[ctx->ev_used], b.stream));
+    FPW_CK(cudaEventRecord(ctx->ev[ctx->ev_used], st));
   }
-  FPW_CK(launch_tile(ta, pl->shape, b.p.phase_mode, acc64, pl->grid, b.stream));
+  FPW_CK(launch_tile(ta, pl->shape, b.p.phase_mode, acc64, pl->grid, st));
   if (timed) {
-    FPW_CK(cudaEventRecord(ctx->ev[ctx->ev_used + 1], b.stream));
+    FPW_CK(cudaEventRecord(ctx->ev[ctx->ev_used + 1], st));
     ctx->ev_used += 2;
   }
   if (b.k > 0) {
@@ -389,9 +393,9 @@ int enqueue_tile_path(fpw_ctx* ctx, const BatchCall& b, Plan* pl, unsigned* word
     ma.k = b.k;
     ma.topk_idx = b.topk_idx;
     ma.topk_S = b.topk_S;
-    FPW_CK(launch_merge(ma, b.stream));
+    FPW_CK(launch_merge(ma, st));
   }
-  FPW_CK(launch_latch(words, b.stream));
+  FPW_CK(launch_latch(words, st));
   return FPW_OK;
 }
 
@@ -418,7 +422,7 @@ int run_tile_path(fpw_ctx* ctx, const BatchCall& b) {
   if (memcmp(before, after, sizeof(before)) != 0) drop_graphs(ctx);
   unsigned* words = static_cast<unsigned*>(ctx->words.p);
 
-  if (!b.p.use_graph) return enqueue_tile_path(ctx, b, pl, words);
+  if (!b.p.use_graph) return enqueue_tile_path(ctx, b, pl, words, b.stream);
 
   uint64_t gk = mix(pl->key, (const void*)b.stream);
   for (const void* q : {(const void*)b.offsets, (const void*)b.t, (const void*)b.x, (const void*)b.sigma,
@@ -444,10 +448,12 @@ int run_tile_path(fpw_ctx* ctx, const BatchCall& b) {
       FPW_CK(cudaGraphLaunch(g.exec, b.stream));
       return FPW_OK;
     }
+  // Capture on the context's own stream (the legacy default stream cannot be
+  // captured); the instantiated graph is launched on the caller's stream.
   cudaGraph_t graph = nullptr;
-  FPW_CK(cudaStreamBeginCapture(b.stream, cudaStreamCaptureModeThreadLocal));
-  rc = enqueue_tile_path(ctx, b, pl, words);
-  cudaError_t ec = cudaStreamEndCapture(b.stream, &graph);
+  FPW_CK(cudaStreamBeginCapture(ctx->own_stream, cudaStreamCaptureModeThreadLocal));
+  rc = enqueue_tile_path(ctx, b, pl, words, ctx->own_stream);
+  cudaError_t ec = cudaStreamEndCapture(ctx->own_stream, &graph);
   if (rc != FPW_OK) {
     if (graph) cudaGraphDestroy(graph);
     return rc;
@@ -700,6 +706,7 @@ int fpw_periodogram_batch_ex(fpw_ctx* ctx, void* stream, const fpw_params* param
   DeviceGuard g(ctx->device);
   if (!g.ok) return FPW_ECUDA;
   std::lock_guard<std::mutex> lk(ctx->mu);
+  clear_stale_error();
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   ctx->last_stream = st;
   if (ncurves == 0) return FPW_OK;
@@ -758,6 +765,7 @@ int fpw_periodogram_ex(fpw_ctx* ctx, void* stream, const fpw_params* params, con
   DeviceGuard g(ctx->device);
   if (!g.ok) return FPW_ECUDA;
   std::lock_guard<std::mutex> lk(ctx->mu);
+  clear_stale_error();
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   ctx->last_stream = st;
   int64_t off_h[2] = {0, n};
@@ -882,6 +890,7 @@ int fpw_debug_bins(fpw_ctx* ctx, void* stream, const fpw_params* params, const d
   DeviceGuard g(ctx->device);
   if (!g.ok) return FPW_ECUDA;
   std::lock_guard<std::mutex> lk(ctx->mu);
+  clear_stale_error();
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   ctx->last_stream = st;
   DebugBinsArgs a{};

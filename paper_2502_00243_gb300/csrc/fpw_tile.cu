@@ -242,10 +242,16 @@ __global__ void __launch_bounds__(512) tile_kernel(const TileArgs args) {
         }
         __syncthreads();
         if (lin && PHASE == FPW_PHASE_FIXED64) {
+          // The next observation's staged data is loaded before this one's bin
+          // stores (the compiler cannot move it there itself: both are shared
+          // memory), so the broadcast-load latency overlaps the bin updates.
+          ulonglong2 pd = sPD[0];
+          A2 aw = sAW[0];
 #pragma unroll 2
           for (int i = 0; i < cnt; ++i) {
-            const ulonglong2 pd = sPD[i];
-            const A2 aw = sAW[i];
+            const int in = (i + 1 < cnt) ? i + 1 : i;
+            const ulonglong2 pdn = sPD[in];
+            const A2 awn = sAW[in];
             unsigned long long phi = pd.x + (unsigned long long)j0 * pd.y;
             unsigned off[R];
 #pragma unroll
@@ -258,6 +264,8 @@ __global__ void __launch_bounds__(512) tile_kernel(const TileArgs args) {
             for (int r = 0; r < R; ++r) v[r] = *reinterpret_cast<const A2*>(my_bins + off[r]);
 #pragma unroll
             for (int r = 0; r < R; ++r) *reinterpret_cast<A2*>(my_bins + off[r]) = acc_add(v[r], aw);
+            pd = pdn;
+            aw = awn;
           }
         } else if (lin) {  // FPW_PHASE_FP32: FP32 phase from an FP32 anchor every K frequencies
           const int K = args.K;

@@ -110,7 +110,7 @@ def test_ragged_batches_dense_and_topk(ctx, case):
         near = oracle.min_edge(t, w.freqs, M) <= 1e-9 if t.size else np.zeros(F, bool)
         bound = s_bound(x, s)
         assert_S_close(Sd[ci], S_or[ci], bound, rel=rel, mask=~near, what=f"case {case} curve {ci} dense")
-        check_topk(idx[ci], Sk[ci], o_idx[ci], o_S[ci], rel=rel, abs_tol=1e-7 * bound, o_dense=S_or[ci],
+        check_topk(idx[ci], Sk[ci], o_idx[ci], o_S[ci], rel=rel, abs_tol=1e-7 * bound, o_dense=S_or[ci], raw=raw,
                    what=f"case {case} curve {ci}")
 
 
