@@ -153,6 +153,30 @@ FPW_API int fpw_periodogram_batch_host(fpw_ctx* ctx, const fpw_params* params, c
                                const double* t, const double* x, const double* sigma, const double* freqs,
                                int64_t nfreq, int M, int k, int32_t* topk_idx, float* topk_S);
 
+/* fpw_periodogram_batch without any device allocation. (The paper has no
+ * counterpart: this is a deployment variant of the batched call.)
+ * For callers that cannot call cudaMalloc: code that runs inside another
+ * framework's memory pool, plugins whose host forbids device allocation after
+ * start-up, and real-time pipelines that must not risk an allocation failure or
+ * an implicit device synchronization mid-run. All scratch memory lives in one
+ * file-scope device array of 32 MiB that every GPU loading the library holds
+ * until the process exits; inputs and outputs are still the caller's.
+ *   Arguments as fpw_periodogram_batch_ex (device pointers; offsets_host is an
+ *   optional host copy of offsets, else offsets[ncurves] is read back), minus
+ *   S_out. One work item per curve. phase_mode FPW_PHASE_FP64 is not supported.
+ *   Limit: 64 + 16*C + 4*(C+1) + C + 12*C*k + 8*(nobs+2) bytes (16*(nobs+2)
+ *   with FPW_ACCUM_FP64), each term rounded up to 256, must fit in 32 MiB
+ *   (about 4 million observations); larger inputs return FPW_EINVAL.
+ *   The first call on a device (with that device current) looks up the
+ *   array's device address; make it before any stream capture. Every call
+ *   shares the array and clears what must start at zero; calls that overlap
+ *   on the GPU race. Synchronizes `stream` before returning.
+ * Errors: FPW_EINVAL, FPW_EDATA, FPW_ENOTSUP, FPW_ECUDA. */
+FPW_API int fpw_periodogram_batch_noalloc(void* stream, const fpw_params* params, const int64_t* offsets,
+                                          const int64_t* offsets_host, int64_t ncurves, const double* t,
+                                          const double* x, const double* sigma, const double* freqs, int64_t nfreq,
+                                          int M, int k, int32_t* topk_idx, float* topk_S);
+
 /* Diagnostic: the phase bin every observation gets at every frequency, computed
  * with the same device phase arithmetic as the periodogram kernels
  * (Appendix A.1 bin definition), for bin-mismatch accounting.

@@ -29,7 +29,7 @@ FPW_MAX_TOPK = 64
 EXPORTED = ("fpw_params_default", "fpw_ctx_create", "fpw_ctx_destroy", "fpw_ctx_status", "fpw_periodogram",
             "fpw_periodogram_ex", "fpw_periodogram_batch", "fpw_periodogram_batch_ex", "fpw_periodogram_batch_host",
             "fpw_debug_bins", "fpw_strerror", "fpw_version", "fpw_last_cuda_error", "fpw_ctx_set_timing",
-            "fpw_ctx_kernel_time")
+            "fpw_ctx_kernel_time", "fpw_periodogram_batch_noalloc")
 
 
 class FPWError(RuntimeError):
@@ -83,6 +83,7 @@ def lib():
                 "fpw_last_cuda_error": (ctypes.c_char_p, []),
                 "fpw_ctx_set_timing": (ci, [vp, ci]),
                 "fpw_ctx_kernel_time": (ci, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
+                "fpw_periodogram_batch_noalloc": (ci, [vp, P, vp, vp, i64, vp, vp, vp, vp, i64, ci, ci, vp, vp]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -273,3 +274,21 @@ def fpw_debug_bins(ctx: Context, stream, params, t, freqs, M: int, bins_out):
                               _dev(bins_out, torch.int32, "bins_out"))
     _check(rc, "fpw_debug_bins")
     return bins_out
+
+
+def fpw_periodogram_batch_noalloc(stream, params, offsets, offsets_host, t, x, sigma, freqs, M: int, k: int, topk_idx,
+                                  topk_S):
+    """The batched call for callers that cannot allocate device memory: the
+    library's scratch is a fixed device array (see include/fpw.h)."""
+    import torch
+    oh = None
+    if offsets_host is not None:
+        offsets_host = np.ascontiguousarray(offsets_host, dtype=np.int64)
+        oh = ctypes.c_void_p(offsets_host.ctypes.data)
+    rc = lib().fpw_periodogram_batch_noalloc(
+        _stream(stream), _params(params), _dev(offsets, torch.int64, "offsets"), oh, offsets.numel() - 1,
+        _dev(t, torch.float64, "t"), _dev(x, torch.float64, "x"), _dev(sigma, torch.float64, "sigma"),
+        _dev(freqs, torch.float64, "freqs"), freqs.numel(), int(M), int(k), _dev(topk_idx, torch.int32, "topk_idx"),
+        _dev(topk_S, torch.float32, "topk_S"))
+    _check(rc, "fpw_periodogram_batch_noalloc")
+    return topk_idx, topk_S
