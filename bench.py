@@ -40,6 +40,7 @@ WORKLOAD = "sweep_100k"
 NSM_NOMINAL = 152
 SM_MAX_MHZ_NOMINAL = 2070.0
 SMEM_EVALS_PER_CLK_SM = 8  # 16 B (A, B) read-modify-write per evaluation at 128 B/clk/SM
+KERNELS_PER_STEP = 5  # prep, tile_dev, tile, merge, latch
 
 
 # ---------------------------------------------------------------- workload generation (spawned workers)
@@ -102,6 +103,25 @@ def subset(batch, ids):
     o[1:] = np.cumsum([b - a for a, b in parts])
     cat = lambda arr: np.concatenate([arr[a:b] for a, b in parts]) if parts else np.zeros(0)
     return o, cat(t), cat(x), cat(s)
+
+
+# ---------------------------------------------------------------- multi-GPU: curves shard across ranks
+def shard_batches(steps, world, rank, nbatches):
+    """Batch processed by this rank at each step: (step * world + rank) mod nbatches.
+    Ranks take disjoint batches within a step (weak scaling: per-rank work is fixed)."""
+    return [(s * world + rank) % nbatches for s in range(steps)]
+
+
+def reduce_timing(dist, device, elapsed_ms, evals):
+    """Across ranks: the max elapsed time and the summed evaluations (no data-path collective)."""
+    import torch
+    if dist is None:
+        return elapsed_ms, evals
+    tt = torch.tensor([elapsed_ms, evals], dtype=torch.float64, device=device)
+    mx = tt.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    dist.all_reduce(tt, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(tt[1])
 
 
 # ---------------------------------------------------------------- clocks
@@ -210,6 +230,44 @@ def oracle_sample(batch, F_grid, M, k, target_s, cores):
     return ids, F_grid[start:start + nf]
 
 
+def precision_sample(G, ctx, batch, F_grid, M, ncurves=6, nwin=4096):
+    """Bins and S of the timed configuration against the FP64 oracle, on a
+    sample: stratified curves x the last nwin grid frequencies."""
+    import numpy as np
+    import torch
+
+    import oracle
+    ids = stratified(batch[0], ncurves)
+    o, t, x, s = subset(batch, ids)
+    fr = F_grid[-nwin:]
+    dev = [torch.from_numpy(a).cuda() for a in (o, t, x, s, fr)]
+    Sd = torch.empty(len(ids) * nwin, dtype=torch.float64, device="cuda")
+    G.fpw_periodogram_batch_ex(ctx, None, None, dev[0], o, dev[1], dev[2], dev[3], dev[4], M, 0, None, None, Sd)
+    S_g = Sd.cpu().numpy().reshape(len(ids), nwin)
+    mism = far = pairs = 0
+    errs, errs_off = [], []
+    for c in range(len(ids)):
+        tc, xc, sc = t[o[c]:o[c + 1]], x[o[c]:o[c + 1]], s[o[c]:o[c + 1]]
+        bins = torch.empty(nwin * tc.size, dtype=torch.int32, device="cuda")
+        G.fpw_debug_bins(ctx, None, None, torch.from_numpy(tc).cuda(), dev[4], M, bins)
+        g = bins.cpu().numpy().reshape(nwin, tc.size)
+        b, e = oracle.bins(tc, fr, M)
+        mm = g != b
+        mism += int(mm.sum())
+        far += int((mm & (e > 1e-9)).sum())
+        pairs += mm.size
+        S_o = oracle.fpw(tc, xc, sc, fr, M)
+        err = np.abs(S_g[c] - S_o) / np.maximum(np.abs(S_o), 1e-300)
+        errs.append(err)
+        errs_off.append(err[~(mm.any(axis=1))])
+    errs, errs_off = np.concatenate(errs), np.concatenate(errs_off)
+    return {"sample": f"{len(ids)} stratified curves x the last {nwin} grid frequencies (f up to 50 1/d)",
+            "bin_mismatch": mism, "pairs": pairs, "bin_mismatch_rate": mism / max(pairs, 1),
+            "mismatch_beyond_1e-9_cycles": far, "S_rel_err_max": float(errs.max()),
+            "S_rel_err_median": float(np.median(errs)),
+            "S_rel_err_max_where_bins_agree": float(errs_off.max()) if errs_off.size else None}
+
+
 # ---------------------------------------------------------------- reference arm: the CPU oracle
 def run_reference(args):
     rank, world, _ = env_rank()
@@ -267,7 +325,7 @@ def run_gb300(args):
     cores = os.cpu_count() or 1
     nb = args.curves_total // args.batch_curves
     steps = args.warmup + args.steps
-    batch_of = [(s * world + rank) % nb for s in range(steps)]
+    batch_of = shard_batches(steps, world, rank, nb)
     ids = sorted(set(batch_of))
     workers = max(1, min(16, cores // max(1, min(world, cores))))
     t_gen = time.perf_counter()
@@ -282,6 +340,10 @@ def run_gb300(args):
     idx = torch.empty(C * k, dtype=torch.int32, device="cuda")
     Sk = torch.empty(C * k, dtype=torch.float32, device="cuda")
     ctx = G.Context(local_rank)
+    tuned = None
+    if args.autotune:
+        from paper_2502_00243_gb300 import autotune
+        tuned = autotune.tune(ctx, Ms=(args.M,))
     params = G.fpw_params_default()
     stream = torch.cuda.current_stream()
 
@@ -322,14 +384,7 @@ def run_gb300(args):
     status = ctx.status()
     if status != 0:
         raise RuntimeError(f"device status {status} in the timed region")
-    if dist:
-        tt = torch.tensor([ms, evals, kern_ms], dtype=torch.float64, device="cuda")
-        mx = tt.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        dist.all_reduce(tt, op=dist.ReduceOp.SUM)
-        ms_max, evals_all = float(mx[0]), float(tt[1])
-    else:
-        ms_max, evals_all = ms, evals
+    ms_max, evals_all = reduce_timing(dist, "cuda", ms, evals)
     value = evals_all / (ms_max / 1e3)
 
     # ---- end to end through the host-buffer entry point (pinned host memory)
@@ -366,12 +421,7 @@ def run_gb300(args):
             h2d += hb
             d2h += db
         dt = time.perf_counter() - t0
-        if dist:
-            tt = torch.tensor([dt, ev_h], dtype=torch.float64, device="cuda")
-            mx = tt.clone()
-            dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-            dist.all_reduce(tt, op=dist.ReduceOp.SUM)
-            dt, ev_h = float(mx[0]), float(tt[1])
+        dt, ev_h = reduce_timing(dist, "cuda", dt, ev_h)
         e2e = {"value": ev_h / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d // args.steps),
                "d2h_bytes_per_step": int(d2h // args.steps), "api": "fpw_periodogram_batch_host"}
 
@@ -401,6 +451,10 @@ def run_gb300(args):
                  f"full grid, M={args.M}, one launch per curve (+1 top-k launch)",
                  "speedup_of_batched_split": value / pval}
 
+    prec = None
+    if rank == 0 and not args.no_precision:
+        prec = precision_sample(G, ctx, host[ids[0]], F_grid, args.M)
+
     # ---- CPU oracle on a bounded sample (rank 0, one GPU only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -427,8 +481,8 @@ def run_gb300(args):
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": config_block(args, nb, mean_ev), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": 4 * args.steps, "clocks": clk, "plain_fp64": plain,
-                "gen_seconds": round(t_gen, 2)}
+                "gpu_launches": KERNELS_PER_STEP * args.steps, "clocks": clk, "plain_fp64": plain,
+                "precision": prec, "gen_seconds": round(t_gen, 2), "autotuned": tuned}
         print(json.dumps(line), flush=True)
     ctx.close()
     if dist:
@@ -454,6 +508,8 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-precision", action="store_true")
+    ap.add_argument("--autotune", action="store_true", help="measure and install tuned kernel shapes before timing")
     args = ap.parse_args(argv)
     if args.warmup < 0 or args.steps < 1:
         ap.error("need --steps >= 1 and --warmup >= 0")

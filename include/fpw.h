@@ -82,7 +82,7 @@ typedef struct fpw_params {
   int K;                /* FPW_PHASE_FP32 only: re-anchor interval in frequencies (default 256) */
   int peak_mode;        /* FPW_PEAK_* (default FPW_PEAK_LOCALMAX) */
   int threads;          /* 0 = tuned; else threads per block (multiple of 32, 32..512) */
-  int freqs_per_thread; /* 0 = tuned; else 2, 4 or 8 */
+  int freqs_per_thread; /* 0 = tuned; else 1, 2, 4 or 8 */
   int obs_chunk;        /* 0 = tuned; else observations staged in shared memory per pass (>= 32) */
   int use_graph;        /* 1 = capture the launch sequence in a CUDA graph and replay it on identical calls */
 } fpw_params;
@@ -186,6 +186,18 @@ FPW_API int fpw_periodogram_batch_noalloc(void* stream, const fpw_params* params
  * that are multiples of params->K (FP32) or of the tile width (FIXED64). */
 FPW_API int fpw_debug_bins(fpw_ctx* ctx, void* stream, const fpw_params* params, const double* t, int64_t n,
                    const double* freqs, int64_t nfreq, int M, int32_t* bins_out);
+
+/* Tuned kernel shapes. Adds a shape -- threads per block (multiple of 32,
+ * 32..512), frequencies per thread (1, 2, 4 or 8) and observations per pass
+ * (0 = largest that keeps two blocks per SM) -- used for batched and single
+ * calls whose bin count lies in [M_lo, M_hi] and whose observation-weighted
+ * mean curve size lies in [n_lo, n_hi). Later entries take precedence; explicit
+ * fpw_params fields override the table. The autotuner
+ * (paper_2502_00243_gb300/autotune.py) measures candidates and fills it.
+ * Errors: FPW_EINVAL for an empty range or an invalid shape. */
+FPW_API int fpw_ctx_set_shape(fpw_ctx* ctx, int M_lo, int M_hi, int64_t n_lo, int64_t n_hi, int threads,
+                              int freqs_per_thread, int obs_chunk);
+FPW_API int fpw_ctx_clear_shapes(fpw_ctx* ctx);
 
 /* Profiling hook. While enabled, the context records a pair of CUDA events on
  * the caller's stream around every launch of the periodogram kernel (the

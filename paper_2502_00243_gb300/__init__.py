@@ -29,7 +29,7 @@ FPW_MAX_TOPK = 64
 EXPORTED = ("fpw_params_default", "fpw_ctx_create", "fpw_ctx_destroy", "fpw_ctx_status", "fpw_periodogram",
             "fpw_periodogram_ex", "fpw_periodogram_batch", "fpw_periodogram_batch_ex", "fpw_periodogram_batch_host",
             "fpw_debug_bins", "fpw_strerror", "fpw_version", "fpw_last_cuda_error", "fpw_ctx_set_timing",
-            "fpw_ctx_kernel_time", "fpw_periodogram_batch_noalloc")
+            "fpw_ctx_kernel_time", "fpw_periodogram_batch_noalloc", "fpw_ctx_set_shape", "fpw_ctx_clear_shapes")
 
 
 class FPWError(RuntimeError):
@@ -84,6 +84,8 @@ def lib():
                 "fpw_ctx_set_timing": (ci, [vp, ci]),
                 "fpw_ctx_kernel_time": (ci, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
                 "fpw_periodogram_batch_noalloc": (ci, [vp, P, vp, vp, i64, vp, vp, vp, vp, i64, ci, ci, vp, vp]),
+                "fpw_ctx_set_shape": (ci, [vp, ci, ci, i64, i64, ci, ci, ci]),
+                "fpw_ctx_clear_shapes": (ci, [vp]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -142,6 +144,14 @@ class Context:
 
     def status(self) -> int:
         return int(lib().fpw_ctx_status(self.handle))
+
+    def set_shape(self, M_lo: int, M_hi: int, n_lo: int, n_hi: int, threads: int, freqs_per_thread: int,
+                  obs_chunk: int = 0) -> None:
+        _check(lib().fpw_ctx_set_shape(self.handle, M_lo, M_hi, n_lo, n_hi, threads, freqs_per_thread, obs_chunk),
+               "fpw_ctx_set_shape")
+
+    def clear_shapes(self) -> None:
+        _check(lib().fpw_ctx_clear_shapes(self.handle), "fpw_ctx_clear_shapes")
 
     def set_timing(self, enable: bool) -> None:
         _check(lib().fpw_ctx_set_timing(self.handle, int(bool(enable))), "fpw_ctx_set_timing")

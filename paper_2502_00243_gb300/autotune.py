@@ -1,0 +1,126 @@
+"""Autotuner for the FPW tile kernel's shape.
+
+For each (bin count M, curve-size bucket) it times candidate shapes -- threads
+per block x frequencies per thread -- on synthetic light curves through the C
+ABI (the library's own timing hook: CUDA events around the tile kernel on its
+stream) and installs the fastest in a context's shape table
+(``fpw_ctx_set_shape``). The table can be saved to / loaded from JSON.
+
+Shapes matter because the kernel is bound by the shared-memory pipe: every
+(thread, frequency) slot holds M (A, B) bin pairs, so M and the frequencies
+per thread R decide how many warps fit per SM (latency hiding) and how many
+per-observation broadcast loads are amortised (R).
+"""
+from __future__ import annotations
+
+import json
+import math
+
+import numpy as np
+
+from . import Context, FPWError, fpw_params_default, fpw_periodogram_batch_ex
+
+CANDIDATES = ((128, 8), (128, 4), (128, 2), (128, 1), (256, 4), (256, 2), (256, 1), (64, 8), (64, 4), (192, 2))
+DEFAULT_MS = (10, 20, 50)
+DEFAULT_BUCKETS = ((0, 300), (300, 1000), (1000, 1 << 40))
+
+
+def m_ranges(Ms):
+    """Split [1, inf) into one M range per tuned M (boundaries at midpoints)."""
+    Ms = sorted(set(int(m) for m in Ms))
+    out = []
+    for i, m in enumerate(Ms):
+        lo = 1 if i == 0 else (Ms[i - 1] + m) // 2 + 1
+        hi = (1 << 30) if i == len(Ms) - 1 else (m + Ms[i + 1]) // 2
+        out.append((m, lo, hi))
+    return out
+
+
+def typical_n(lo, hi):
+    hi = min(hi, 3000)
+    lo = max(lo, 50)
+    return int(round(math.sqrt(lo * hi))) if hi > lo else lo
+
+
+def synthetic_curves(n, ncurves, seed=0):
+    """Random light curves of n observations each (times over 1000 d)."""
+    rng = np.random.default_rng(seed)
+    offsets = np.arange(ncurves + 1, dtype=np.int64) * n
+    t = np.sort(rng.uniform(0.0, 1000.0, (ncurves, n)), axis=1).ravel()
+    sigma = np.exp(rng.uniform(np.log(0.01), np.log(0.3), ncurves * n))
+    x = rng.normal(0.0, 1.0, ncurves * n) * sigma
+    return offsets, t, x, sigma
+
+
+def measure(ctx, dev, offsets_h, freqs, M, k, T, R, reps=2):
+    """Mean tile-kernel milliseconds for one shape, or None if it does not fit."""
+    import torch
+    C = offsets_h.shape[0] - 1
+    idx = torch.empty(C * k, dtype=torch.int32, device="cuda")
+    S = torch.empty(C * k, dtype=torch.float32, device="cuda")
+    p = fpw_params_default(threads=T, freqs_per_thread=R)
+    try:
+        fpw_periodogram_batch_ex(ctx, None, p, dev[0], offsets_h, dev[1], dev[2], dev[3], freqs, M, k, idx, S)
+        torch.cuda.synchronize()
+        ctx.set_timing(True)
+        ctx.kernel_time()
+        for _ in range(reps):
+            fpw_periodogram_batch_ex(ctx, None, p, dev[0], offsets_h, dev[1], dev[2], dev[3], freqs, M, k, idx, S)
+        torch.cuda.synchronize()
+        ms, n = ctx.kernel_time()
+    except FPWError:
+        return None
+    finally:
+        ctx.set_timing(False)
+    return ms / max(n, 1)
+
+
+def tune(ctx: Context, Ms=DEFAULT_MS, buckets=DEFAULT_BUCKETS, *, nfreq=50_000, evals_per_case=1.5e10, k=5,
+         candidates=CANDIDATES, apply=True, log=None):
+    """Measure every candidate shape per (M, bucket); returns the table entries
+    (and installs them in ``ctx`` when ``apply``)."""
+    import torch
+    freqs = torch.linspace(0.01, 50.0, nfreq, dtype=torch.float64, device="cuda")
+    entries = []
+    for M, m_lo, m_hi in m_ranges(Ms):
+        for b_lo, b_hi in buckets:
+            n = typical_n(b_lo, b_hi)
+            ncurves = max(8, int(evals_per_case / (n * nfreq)))
+            off, t, x, s = synthetic_curves(n, ncurves, seed=M * 7919 + n)
+            dev = [torch.from_numpy(a).cuda() for a in (off, t, x, s)]
+            evals = float(off[-1]) * nfreq
+            best = None
+            for T, R in candidates:
+                ms = measure(ctx, dev, off, freqs, M, k, T, R)
+                if ms is None:
+                    continue
+                rate = evals / (ms / 1e3)
+                if log:
+                    log(f"M={M} n={n} T={T} R={R}: {rate / 1e9:.1f} Geval/s")
+                if best is None or rate > best[2]:
+                    best = (T, R, rate)
+            if best is None:
+                continue
+            e = {"M_lo": m_lo, "M_hi": m_hi, "n_lo": int(b_lo), "n_hi": int(min(b_hi, 1 << 40)), "threads": best[0],
+                 "freqs_per_thread": best[1], "obs_chunk": 0, "geval_s": best[2] / 1e9, "M": M, "n": n}
+            entries.append(e)
+    if apply:
+        install(ctx, entries)
+    return entries
+
+
+def install(ctx: Context, entries) -> None:
+    for e in entries:
+        ctx.set_shape(e["M_lo"], e["M_hi"], e["n_lo"], e["n_hi"], e["threads"], e["freqs_per_thread"],
+                      e.get("obs_chunk", 0))
+
+
+def save(entries, path: str) -> None:
+    with open(path, "w") as fh:
+        json.dump({"version": 1, "entries": entries}, fh, indent=1)
+
+
+def load(path: str):
+    with open(path) as fh:
+        data = json.load(fh)
+    return data["entries"]

@@ -49,6 +49,7 @@ struct TileArgs {
   int K;                     // FPW_PHASE_FP32 re-anchor interval
   int obs_chunk;             // observations staged per pass
   double inv_alpha2;
+  const double* tile_dev;    // per-tile grid deviation (tile_dev_kernel), or NULL: checked in the tile kernel
 };
 
 struct PrepArgs {
@@ -127,6 +128,8 @@ bool tile_supported_R(int R);
 cudaError_t launch_tile(const TileArgs& a, const TileShape& s, int phase_mode, bool accum64, int grid,
                         cudaStream_t st);
 cudaError_t launch_prep(const PrepArgs& a, cudaStream_t st);
+// Per-tile grid deviation for tiles of width W starting at q*(W-2)-1, q < tiles.
+cudaError_t launch_tile_dev(const double* freqs, int64_t F, int W, int64_t tiles, double* dev, cudaStream_t st);
 cudaError_t launch_merge(const MergeArgs& a, cudaStream_t st);
 cudaError_t launch_plain(const PlainArgs& a, cudaStream_t st);
 cudaError_t launch_dense_topk(const DenseTopkArgs& a, cudaStream_t st);

@@ -95,6 +95,14 @@ struct Plan {
   uint64_t use = 0;
 };
 
+// A tuned kernel shape for bin counts in [M_lo, M_hi] and a typical curve size
+// (observation-weighted mean N) in [n_lo, n_hi).
+struct ShapeEntry {
+  int M_lo, M_hi;
+  int64_t n_lo, n_hi;
+  int T, R, NC;
+};
+
 struct GraphEntry {
   uint64_t key = 0;
   cudaGraphExec_t exec = nullptr;
@@ -114,11 +122,12 @@ struct fpw_ctx {
   std::mutex mu;
   cudaStream_t last_stream = nullptr;
   cudaStream_t own_stream = nullptr;
-  DevBuf aw, cand_S, cand_idx, curve_bad, words, dense;
+  DevBuf aw, cand_S, cand_idx, curve_bad, words, dense, tile_dev;
   DevBuf h_off, h_t, h_x, h_sigma, h_freqs, h_idx, h_S;  // device copies for the host entry point
   std::vector<int64_t> off_host;                          // host copy of offsets (when not supplied)
   std::vector<Plan*> plans;
   std::vector<GraphEntry> graphs;
+  std::vector<ShapeEntry> shapes;  // tuned shapes (latest entry wins)
   uint64_t tick = 0;
   bool timing = false;
   std::vector<cudaEvent_t> ev;  // pairs (start, stop) of recorded tile launches
@@ -158,22 +167,45 @@ bool valid_params(const fpw_params& p) {
 
 // Kernel shape: T threads, R frequencies per thread, NC observations per pass.
 // Per-thread bins take R*M*T*(8|16) bytes; the observation chunk takes
-// NC*(16 + 8|16) bytes. Prefer two resident blocks per SM (one stages while the
-// other accumulates); fall back to one when the bins alone do not allow it.
-int choose_shape(fpw_ctx* ctx, const fpw_params& p, int M, int k, int64_t max_n, TileShape& out) {
+// NC*(16 + 8|16) bytes. Precedence: explicit params > the context's tuned
+// table (fpw_ctx_set_shape) > the built-in defaults, which were measured on a
+// GB300 with ZTF-like curves (threads x frequencies-per-thread sweeps at
+// M = 10, 20, 50): R = 8 for M <= 12, R = 4 for M <= 24 (R = 2 when the
+// typical curve has fewer than 300 observations), R = 2 up to M = 64, R = 1
+// beyond, T = 128 (halved while the bins alone do not fit). NC: the largest
+// chunk that keeps two resident blocks per SM (one stages while the other
+// accumulates), else one block per SM.
+int choose_shape(fpw_ctx* ctx, const fpw_params& p, int M, int k, int64_t max_n, int64_t n_typ, TileShape& out) {
   const bool acc64 = p.accum == FPW_ACCUM_FP64;
-  const int T = p.threads ? p.threads : 128;
-  int R = p.freqs_per_thread;
-  if (!R) R = acc64 ? 2 : (M <= 24 ? 4 : 2);
+  int T = 128, R = 4, NC = 0;
+  if (acc64)
+    R = 2;
+  else if (M <= 12)
+    R = 8;
+  else if (M <= 24)
+    R = n_typ < 300 ? 2 : 4;
+  else if (M <= 64)
+    R = 2;
+  else
+    R = 1;
+  for (const ShapeEntry& e : ctx->shapes)
+    if (M >= e.M_lo && M <= e.M_hi && n_typ >= e.n_lo && n_typ < e.n_hi) {
+      T = e.T;
+      R = e.R;
+      NC = e.NC;
+    }
+  if (p.threads) T = p.threads;
+  if (p.freqs_per_thread) R = p.freqs_per_thread;
+  if (p.obs_chunk) NC = p.obs_chunk;
+  const bool fixedT = p.threads != 0;
+  while (!fixedT && T > 32 && tile_smem_bytes(T, R, M, 32, k, acc64) > (size_t)ctx->smem_optin) T /= 2;
   const int64_t want_nc = std::max<int64_t>(32, ((max_n + 31) / 32) * 32);
   const size_t per_sm = (size_t)ctx->smem_per_sm;
   auto fits = [&](int blocks, int nc) {
     const size_t s = tile_smem_bytes(T, R, M, nc, k, acc64);
     return s <= (size_t)ctx->smem_optin && (s + 1024) * blocks <= per_sm;
   };
-  int NC = p.obs_chunk;
   if (!NC) {
-    NC = 0;
     for (int blocks : {2, 1}) {
       int lo = 32, hi = (int)std::min<int64_t>(want_nc, 1 << 16);
       if (!fits(blocks, lo)) continue;
@@ -347,6 +379,9 @@ int enqueue_tile_path(fpw_ctx* ctx, const BatchCall& b, Plan* pl, unsigned* word
   pa.curve_bad = static_cast<uint8_t*>(ctx->curve_bad.p);
   pa.status = words + 1;
   FPW_CK(launch_prep(pa, st));
+  const int W = pl->shape.threads * pl->shape.R;
+  const int64_t tiles = (b.F + (W - 2) - 1) / (W - 2);
+  FPW_CK(launch_tile_dev(b.freqs, b.F, W, tiles, static_cast<double*>(ctx->tile_dev.p), st));
   TileArgs ta{};
   ta.t = b.t;
   ta.offsets = b.offsets;
@@ -368,6 +403,7 @@ int enqueue_tile_path(fpw_ctx* ctx, const BatchCall& b, Plan* pl, unsigned* word
   ta.K = b.p.K;
   ta.obs_chunk = pl->shape.obs_chunk;
   ta.inv_alpha2 = b.p.inv_alpha2;
+  ta.tile_dev = static_cast<const double*>(ctx->tile_dev.p);
   const bool timed = ctx->timing && !b.p.use_graph;
   if (timed) {
     while (ctx->ev.size() < ctx->ev_used + 2) {
@@ -402,9 +438,16 @@ int enqueue_tile_path(fpw_ctx* ctx, const BatchCall& b, Plan* pl, unsigned* word
 int run_tile_path(fpw_ctx* ctx, const BatchCall& b) {
   const bool acc64 = b.p.accum == FPW_ACCUM_FP64;
   int64_t max_n = 0;
-  for (int64_t c = 0; c < b.C; ++c) max_n = std::max(max_n, b.off_h[c + 1] - b.off_h[c]);
+  double sn = 0.0, sn2 = 0.0;
+  for (int64_t c = 0; c < b.C; ++c) {
+    const int64_t n = b.off_h[c + 1] - b.off_h[c];
+    max_n = std::max(max_n, n);
+    sn += (double)n;
+    sn2 += (double)n * (double)n;
+  }
+  const int64_t n_typ = sn > 0.0 ? (int64_t)(sn2 / sn) : 0;  // observation-weighted mean curve size
   TileShape sh{};
-  int rc = choose_shape(ctx, b.p, b.M, b.k, max_n, sh);
+  int rc = choose_shape(ctx, b.p, b.M, b.k, max_n, n_typ, sh);
   if (rc != FPW_OK) return rc;
   const int bps = tile_max_blocks_per_sm(sh.R, b.p.phase_mode, acc64, sh.threads, sh.smem);
   if (bps < 1) return FPW_ENOTSUP;
@@ -412,13 +455,17 @@ int run_tile_path(fpw_ctx* ctx, const BatchCall& b) {
   if (!pl) return rc;
   const int64_t nobs = b.off_h[b.C];
   // scratch (grow-only; growing invalidates captured graphs)
-  void* before[5] = {ctx->aw.p, ctx->cand_S.p, ctx->cand_idx.p, ctx->curve_bad.p, ctx->words.p};
+  void* before[6] = {ctx->aw.p, ctx->cand_S.p, ctx->cand_idx.p, ctx->curve_bad.p, ctx->words.p, ctx->tile_dev.p};
   cudaError_t e = ensure(ctx->aw, (size_t)(nobs + 2) * (acc64 ? 16 : 8));
+  {
+    const int64_t Wown = (int64_t)sh.threads * sh.R - 2;
+    if (e == cudaSuccess) e = ensure(ctx->tile_dev, sizeof(double) * (size_t)((b.F + Wown - 1) / Wown + 1));
+  }
   if (e == cudaSuccess && b.k > 0) e = ensure(ctx->cand_S, (size_t)pl->nslots * b.k * sizeof(double));
   if (e == cudaSuccess && b.k > 0) e = ensure(ctx->cand_idx, (size_t)pl->nslots * b.k * sizeof(int32_t));
   if (e == cudaSuccess) e = ensure(ctx->curve_bad, (size_t)b.C + 16);
   if (e != cudaSuccess) return cuda_fail(e, "scratch allocation");
-  void* after[5] = {ctx->aw.p, ctx->cand_S.p, ctx->cand_idx.p, ctx->curve_bad.p, ctx->words.p};
+  void* after[6] = {ctx->aw.p, ctx->cand_S.p, ctx->cand_idx.p, ctx->curve_bad.p, ctx->words.p, ctx->tile_dev.p};
   if (memcmp(before, after, sizeof(before)) != 0) drop_graphs(ctx);
   unsigned* words = static_cast<unsigned*>(ctx->words.p);
 
@@ -441,6 +488,7 @@ int run_tile_path(fpw_ctx* ctx, const BatchCall& b) {
   gk = mix(gk, ctx->cand_S.p);
   gk = mix(gk, ctx->cand_idx.p);
   gk = mix(gk, ctx->curve_bad.p);
+  gk = mix(gk, ctx->tile_dev.p);
   gk = mix(gk, pl);
   for (GraphEntry& g : ctx->graphs)
     if (g.key == gk) {
@@ -646,13 +694,31 @@ int fpw_ctx_destroy(fpw_ctx* ctx) {
       delete p;
     }
     ctx->plans.clear();
-    for (DevBuf* b : {&ctx->aw, &ctx->cand_S, &ctx->cand_idx, &ctx->curve_bad, &ctx->words, &ctx->dense, &ctx->h_off,
+    for (DevBuf* b : {&ctx->aw, &ctx->cand_S, &ctx->cand_idx, &ctx->curve_bad, &ctx->words, &ctx->dense, &ctx->tile_dev, &ctx->h_off,
                       &ctx->h_t, &ctx->h_x, &ctx->h_sigma, &ctx->h_freqs, &ctx->h_idx, &ctx->h_S})
       free_buf(*b);
     if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
     for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
   }
   delete ctx;
+  return FPW_OK;
+}
+
+int fpw_ctx_set_shape(fpw_ctx* ctx, int M_lo, int M_hi, int64_t n_lo, int64_t n_hi, int threads, int freqs_per_thread,
+                      int obs_chunk) {
+  if (!ctx || M_lo < 1 || M_hi < M_lo || n_lo < 0 || n_hi <= n_lo) return FPW_EINVAL;
+  if (threads < 32 || threads > 512 || threads % 32 != 0 || !tile_supported_R(freqs_per_thread)) return FPW_EINVAL;
+  if (obs_chunk != 0 && obs_chunk < 32) return FPW_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  ShapeEntry e{M_lo, M_hi, n_lo, n_hi, threads, freqs_per_thread, obs_chunk};
+  ctx->shapes.push_back(e);
+  return FPW_OK;
+}
+
+int fpw_ctx_clear_shapes(fpw_ctx* ctx) {
+  if (!ctx) return FPW_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  ctx->shapes.clear();
   return FPW_OK;
 }
 

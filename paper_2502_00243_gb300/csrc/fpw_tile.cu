@@ -47,6 +47,14 @@ __device__ __forceinline__ double2 acc_add(double2 a, double2 b) { return make_d
 __device__ __forceinline__ void acc_zero(float2& v) { v = make_float2(0.f, 0.f); }
 __device__ __forceinline__ void acc_zero(double2& v) { v = make_double2(0.0, 0.0); }
 
+// n / d for the reduce step: the fast reciprocal-based quotient (2 ulp) in the
+// normal range of d, correctly rounded division elsewhere; binary64 always
+// correctly rounded.
+__device__ __forceinline__ float quotient(float n, float d) {
+  return (d >= 1.17549435e-38f && d <= 8.5e37f) ? __fdividef(n, d) : n / d;
+}
+__device__ __forceinline__ double quotient(double n, double d) { return n / d; }
+
 struct Layout {
   size_t bins, pd, aw, candS, candI, topS, topI, edges, red, misc, total;
 };
@@ -208,38 +216,57 @@ __global__ void __launch_bounds__(512) tile_kernel(const TileArgs args) {
     __syncthreads();
     tm = 0.0;
     for (int w = 0; w < nwarps; ++w) tm = fmax(tm, red[w]);
+    const bool resident = n <= NC;
+    bool staged_lin = false;
 
     for (int64_t s = (int64_t)wi.f_lo - 1; s + 1 < wi.f_hi; s += W - 2) {
       const int64_t a = s < 0 ? 0 : s;
       const double fa = args.freqs[a];
-      // grid linearity over this tile
-      bool nonlin = false;
+      // grid linearity over this tile: the precomputed per-tile deviation when
+      // available (tile starts sit at multiples of W-2, minus one), else checked here
+      bool lin;
+      if (args.tile_dev) {
+        lin = args.tile_dev[(s + 1) / (W - 2)] * tm <= kGridTolCycles;
+      } else {
+        bool nonlin = false;
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const int64_t k = s + (int64_t)j0 + r;
-        if (k >= 0 && k < F) {
-          const double pred = fma((double)(k - a), df, fa);
-          if (fabs(args.freqs[k] - pred) * tm > kGridTolCycles) nonlin = true;
+        for (int r = 0; r < R; ++r) {
+          const int64_t k = s + (int64_t)j0 + r;
+          if (k >= 0 && k < F) {
+            const double pred = fma((double)(k - a), df, fa);
+            if (fabs(args.freqs[k] - pred) * tm > kGridTolCycles) nonlin = true;
+          }
         }
+        lin = !__syncthreads_or(nonlin);
       }
-      const bool lin = !__syncthreads_or(nonlin);
+      // a curve that fits in one chunk keeps D_i and (a_i, w_i) staged across the
+      // tiles of an item; only the anchor phase is recomputed per tile
+      const bool keep = resident && staged_lin && lin;
 
       for (int64_t o = 0; o < n; o += NC) {
         const int cnt = (int)((n - o) < NC ? (n - o) : NC);
         for (int i = tid; i < cnt; i += T) {
           const double ti = args.t[base + o + i];
-          ulonglong2 pd;
-          if (lin) {
-            const unsigned long long D = phase_fixed64(ti, df);
+          if (keep) {
+            const unsigned long long D = sPD[i].y;
             unsigned long long P = phase_fixed64(ti, fa);
             if (s < a) P -= D;  // tile starts one step before frequency 0
-            pd = make_ulonglong2(P, D);
+            sPD[i].x = P;
           } else {
-            pd = make_ulonglong2((unsigned long long)__double_as_longlong(ti), 0ull);
+            ulonglong2 pd;
+            if (lin) {
+              const unsigned long long D = phase_fixed64(ti, df);
+              unsigned long long P = phase_fixed64(ti, fa);
+              if (s < a) P -= D;
+              pd = make_ulonglong2(P, D);
+            } else {
+              pd = make_ulonglong2((unsigned long long)__double_as_longlong(ti), 0ull);
+            }
+            sPD[i] = pd;
+            sAW[i] = reinterpret_cast<const A2*>(args.aw)[base + o + i];
           }
-          sPD[i] = pd;
-          sAW[i] = reinterpret_cast<const A2*>(args.aw)[base + o + i];
         }
+        staged_lin = lin;
         __syncthreads();
         if (lin && PHASE == FPW_PHASE_FIXED64) {
           // The next observation's staged data is loaded before this one's bin
@@ -323,8 +350,9 @@ __global__ void __launch_bounds__(512) tile_kernel(const TileArgs args) {
         __syncthreads();
       }
 
-      // reduce to S (and clear the bins for the next tile)
-      double S[R];
+      // reduce to S (and clear the bins for the next tile); S and the peak test
+      // stay in the accumulation type (no binary64 work for FP32 sums)
+      A S[R];
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         A acc = (A)0;
@@ -336,10 +364,10 @@ __global__ void __launch_bounds__(512) tile_kernel(const TileArgs args) {
           acc_zero(z);
           *p = z;
           const A den = v.y + cal;
-          acc += (den > (A)0) ? (v.x * v.x) / den : (A)0;
+          acc += (den > (A)0) ? quotient(v.x * v.x, den) : (A)0;
         }
         const int64_t k = s + (int64_t)j0 + r;
-        S[r] = (k >= 0 && k < F) ? (double)acc : -INFINITY;
+        S[r] = (k >= 0 && k < F) ? acc : (A)-INFINITY;
       }
       // dense output of owned frequencies
       if (args.S_out) {
@@ -347,30 +375,31 @@ __global__ void __launch_bounds__(512) tile_kernel(const TileArgs args) {
         for (int r = 0; r < R; ++r) {
           const int j = (int)j0 + r;
           const int64_t k = s + j;
-          if (j > 0 && j < W - 1 && k >= wi.f_lo && k < wi.f_hi) args.S_out[(int64_t)c * F + k] = S[r];
+          if (j > 0 && j < W - 1 && k >= wi.f_lo && k < wi.f_hi) args.S_out[(int64_t)c * F + k] = (double)S[r];
         }
       }
       if (kk > 0) {
         // neighbours across lanes and warps
-        double left = __shfl_up_sync(0xffffffffu, S[R - 1], 1);
-        double right = __shfl_down_sync(0xffffffffu, S[0], 1);
-        if (lane == 0) edges[2 * warp] = S[0];
-        if (lane == 31) edges[2 * warp + 1] = S[R - 1];
+        A left = __shfl_up_sync(0xffffffffu, S[R - 1], 1);
+        A right = __shfl_down_sync(0xffffffffu, S[0], 1);
+        A* const aedges = reinterpret_cast<A*>(edges);
+        if (lane == 0) aedges[2 * warp] = S[0];
+        if (lane == 31) aedges[2 * warp + 1] = S[R - 1];
         __syncthreads();
-        if (lane == 0) left = (warp > 0) ? edges[2 * warp - 1] : -INFINITY;
-        if (lane == 31) right = (warp + 1 < nwarps) ? edges[2 * warp + 2] : -INFINITY;
-        const double thr = (topI[kk - 1] >= 0) ? topS[kk - 1] : -INFINITY;
+        if (lane == 0) left = (warp > 0) ? aedges[2 * warp - 1] : (A)-INFINITY;
+        if (lane == 31) right = (warp + 1 < nwarps) ? aedges[2 * warp + 2] : (A)-INFINITY;
+        const A thr = (topI[kk - 1] >= 0) ? (A)topS[kk - 1] : (A)-INFINITY;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
           const int j = (int)j0 + r;
           const int64_t k = s + j;
           const bool owned = j > 0 && j < W - 1 && k >= wi.f_lo && k < wi.f_hi;
-          const double prev = (r > 0) ? S[r > 0 ? r - 1 : 0] : left;
-          const double next = (r < R - 1) ? S[r < R - 1 ? r + 1 : 0] : right;
+          const A prev = (r > 0) ? S[r > 0 ? r - 1 : 0] : left;
+          const A next = (r < R - 1) ? S[r < R - 1 ? r + 1 : 0] : right;
           const bool peak = args.peak_raw ? owned : (owned && S[r] > prev && S[r] >= next);
           if (peak && S[r] > thr) {
             const int slot = atomicAdd(&misc[1], 1);
-            candS[slot] = S[r];
+            candS[slot] = (double)S[r];
             candI[slot] = (int)k;
           }
         }
@@ -393,6 +422,27 @@ __global__ void __launch_bounds__(512) tile_kernel(const TileArgs args) {
   }
 }
 
+// Per tile q (start s = q*Wown - 1, width W = Wown + 2): the largest deviation
+// of the grid from the line through f_a (a = max(s, 0)) with step df, the
+// linear prediction used by the tile kernel's fixed-point stepping.
+__global__ void tile_dev_kernel(const double* freqs, int64_t F, int W, int64_t tiles, double* dev) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const double df = (F > 1) ? (freqs[F - 1] - freqs[0]) / (double)(F - 1) : 0.0;
+  for (int64_t q = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); q < tiles; q += warps) {
+    const int64_t s = q * (W - 2) - 1;
+    const int64_t a = s < 0 ? 0 : s;
+    const double fa = freqs[a];
+    double d = 0.0;
+    for (int j = lane; j < W; j += 32) {
+      const int64_t k = s + j;
+      if (k >= 0 && k < F) d = fmax(d, fabs(freqs[k] - fma((double)(k - a), df, fa)));
+    }
+    d = warp_max(d);
+    if (lane == 0) dev[q] = d;
+  }
+}
+
 template <int R, int PHASE, typename A>
 const void* tile_fn() {
   return reinterpret_cast<const void*>(&tile_kernel<R, PHASE, A>);
@@ -405,6 +455,7 @@ const void* pick(int R, int phase_mode, bool acc64) {
     if (acc64) return fp32p ? tile_fn<RR, FPW_PHASE_FP32, double>() : tile_fn<RR, FPW_PHASE_FIXED64, double>(); \
     return fp32p ? tile_fn<RR, FPW_PHASE_FP32, float>() : tile_fn<RR, FPW_PHASE_FIXED64, float>();    \
   }
+  FPW_PICK(1)
   FPW_PICK(2)
   FPW_PICK(4)
   FPW_PICK(8)
@@ -418,10 +469,10 @@ size_t tile_smem_bytes(int T, int R, int M, int NC, int /*k*/, bool accum64) {
   return tile_layout(T, R, M, NC, accum64).total;
 }
 
-bool tile_supported_R(int R) { return R == 2 || R == 4 || R == 8; }
+bool tile_supported_R(int R) { return R == 1 || R == 2 || R == 4 || R == 8; }
 
 cudaError_t tile_init_attributes(int max_smem) {
-  for (int R : {2, 4, 8})
+  for (int R : {1, 2, 4, 8})
     for (int ph : {FPW_PHASE_FIXED64, FPW_PHASE_FP32})
       for (int acc : {0, 1}) {
         cudaError_t e = cudaFuncSetAttribute(pick(R, ph, acc != 0), cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
@@ -436,6 +487,14 @@ int tile_max_blocks_per_sm(int R, int phase_mode, bool accum64, int T, size_t sm
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, T, smem) != cudaSuccess) return 0;
   return nb;
+}
+
+cudaError_t launch_tile_dev(const double* freqs, int64_t F, int W, int64_t tiles, double* dev, cudaStream_t st) {
+  if (tiles <= 0) return cudaSuccess;
+  int64_t blocks = (tiles + 7) / 8;
+  blocks = blocks > 4096 ? 4096 : blocks;
+  tile_dev_kernel<<<(unsigned)blocks, 256, 0, st>>>(freqs, F, W, tiles, dev);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_tile(const TileArgs& a, const TileShape& s, int phase_mode, bool accum64, int grid,
