@@ -19,6 +19,8 @@ Functions and the passages they follow:
 * :func:`fpw_batch` -- the same for a ragged batch (CSR offsets), threads over
   curves, optional dense S and per-curve top-k peaks (Section 3.5
   post-processing).
+* :func:`fpw_multi` -- Section 3.4: S for M = M_max / g from the M_max-bin sums,
+  for each of the g bin offsets.
 * :func:`topk` -- the k highest local maxima of a periodogram (Section 3.5).
 * :func:`bins` -- bin of every (frequency, observation) pair and the exact
   distance from t*f to the nearest bin edge, for bin-mismatch accounting.
@@ -74,6 +76,8 @@ def _load():
             lib.oracle_topk.restype = c_int
             lib.oracle_bins.argtypes = [vp, i64, vp, i64, c_int, vp, vp]
             lib.oracle_bins.restype = c_int
+            lib.oracle_fpw_multi.argtypes = [vp, vp, vp, i64, vp, i64, c_int, c_int, d, vp]
+            lib.oracle_fpw_multi.restype = c_int
             lib.oracle_min_edge.argtypes = [vp, i64, vp, i64, c_int, vp]
             lib.oracle_min_edge.restype = c_int
             lib.oracle_version.restype = c_int
@@ -104,6 +108,17 @@ def fpw(t, x, sigma, freqs, M: int, inv_alpha2: float = 0.0) -> np.ndarray:
     S = np.empty(freqs.shape[0], dtype=np.float64)
     _check(lib.oracle_fpw(_ptr(t), _ptr(x), _ptr(sigma), n, _ptr(freqs), freqs.shape[0], int(M), float(inv_alpha2),
                           _ptr(S)))
+    return S
+
+
+def fpw_multi(t, x, sigma, freqs, M_max: int, g: int, inv_alpha2: float = 0.0) -> np.ndarray:
+    """Section 3.4: S for M = M_max / g bins, combined from the M_max-bin sums,
+    for each of the g bin offsets: array ``[g, F]``."""
+    lib = _load()
+    t, x, sigma, freqs = _f64(t), _f64(x), _f64(sigma), _f64(freqs)
+    S = np.empty((int(g), freqs.shape[0]), dtype=np.float64)
+    _check(lib.oracle_fpw_multi(_ptr(t), _ptr(x), _ptr(sigma), t.shape[0], _ptr(freqs), freqs.shape[0], int(M_max),
+                                int(g), float(inv_alpha2), _ptr(S)))
     return S
 
 

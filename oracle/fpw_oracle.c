@@ -115,6 +115,58 @@ int oracle_fpw(const double* t, const double* x, const double* sigma, int64_t n,
   return ORACLE_OK;
 }
 
+/* Section 3.4, S_FPW for several numbers of bins from one pass: the bin sums
+ * at M_max bins are combined into M = M_max / g bins, for each of the g bin
+ * offsets o: combined bin j of offset o holds the M_max-bins
+ * (j g + o + u) mod M_max, u = 0..g-1. Output S_out[o * nfreq + k], o < g.
+ * (The offset shifts every combined bin edge by o / M_max of a cycle.) */
+int oracle_fpw_multi(const double* t, const double* x, const double* sigma, int64_t n, const double* freqs,
+                     int64_t nfreq, int M_max, int g, double inv_alpha2, double* S_out) {
+  if (n < 0 || nfreq < 0 || M_max < 1 || g < 1 || M_max % g != 0 || !(inv_alpha2 >= 0.0)) return ORACLE_EINVAL;
+  if (nfreq > 0 && (!freqs || !S_out)) return ORACLE_EINVAL;
+  if (n > 0 && (!t || !x || !sigma)) return ORACLE_EINVAL;
+  for (int64_t k = 0; k < nfreq; ++k)
+    if (!isfinite(freqs[k])) return ORACLE_EDATA;
+  if (check_curve(t, x, sigma, n) != ORACLE_OK) return ORACLE_EDATA;
+  const int M = M_max / g;
+  double* A = (double*)malloc(sizeof(double) * (size_t)M_max);
+  double* B = (double*)malloc(sizeof(double) * (size_t)M_max);
+  if (!A || !B) {
+    free(A);
+    free(B);
+    return ORACLE_ENOMEM;
+  }
+  for (int64_t k = 0; k < nfreq; ++k) {
+    for (int m = 0; m < M_max; ++m) {
+      A[m] = 0.0;
+      B[m] = 0.0;
+    }
+    for (int64_t i = 0; i < n; ++i) {
+      double w = 1.0 / (sigma[i] * sigma[i]);
+      int m = oracle_bin(t[i], freqs[k], M_max);
+      A[m] += x[i] * w;
+      B[m] += w;
+    }
+    for (int o = 0; o < g; ++o) {
+      double S = 0.0;
+      for (int j = 0; j < M; ++j) {
+        double a = 0.0, b = 0.0;
+        for (int u = 0; u < g; ++u) {
+          int m = (j * g + o + u) % M_max;
+          a += A[m];
+          b += B[m];
+        }
+        double den = b + inv_alpha2;
+        if (den > 0.0) S += (a * a) / den;
+      }
+      S_out[(int64_t)o * nfreq + k] = S;
+    }
+  }
+  free(A);
+  free(B);
+  return ORACLE_OK;
+}
+
 /* Peaks of a periodogram (Section 3.5 post-processing, reading above). */
 static int is_peak(const double* S, int64_t nfreq, int64_t k) {
   if (nfreq == 1) return 1;

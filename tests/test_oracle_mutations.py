@@ -14,7 +14,11 @@ import tempfile
 import numpy as np
 import pytest
 
-from test_oracle_pins import (GOLDEN, dense_chi2_difference, exact_bins, least_squares_reduction, tiny_case)
+import math
+from fractions import Fraction
+
+from test_oracle_pins import (GOLDEN, dense_chi2_difference, exact_bins, exact_phase, least_squares_reduction,
+                              tiny_case)
 
 SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "oracle", "fpw_oracle.c")
 
@@ -31,6 +35,8 @@ MUTATIONS = {
     "peak_left_nonstrict": ("return S[k] > S[k - 1] && S[k] >= S[k + 1];", "return S[k] >= S[k - 1] && S[k] >= S[k + 1];"),
     "tie_to_higher_index": ("return k1 < k2;", "return k1 > k2;"),
     "ends_never_peaks": ("if (k == 0) return S[0] >= S[1];", "if (k == 0) return 0;"),
+    "multi_ignores_offset": ("int m = (j * g + o + u) % M_max;", "int m = (j * g + u) % M_max;"),
+    "multi_offset_backwards": ("int m = (j * g + o + u) % M_max;", "int m = (j * g - o + u + M_max) % M_max;"),
     "edge_distance_drops_product_error": ("return fabs(r + (ue + (double)M * e)) / (double)M;",
                                           "return fabs(r + ue) / (double)M;"),
 }
@@ -43,7 +49,16 @@ class Api:
         lib.oracle_fpw.argtypes = [vp, vp, vp, i64, vp, i64, ci, d, vp]
         lib.oracle_topk.argtypes = [vp, i64, ci, ci, vp, vp]
         lib.oracle_bins.argtypes = [vp, i64, vp, i64, ci, vp, vp]
+        lib.oracle_fpw_multi.argtypes = [vp, vp, vp, i64, vp, i64, ci, ci, d, vp]
         self.lib = lib
+
+    def fpw_multi(self, t, x, sigma, freqs, M_max, g, c=0.0):
+        t, x, sigma, freqs = (np.ascontiguousarray(a, dtype=np.float64) for a in (t, x, sigma, freqs))
+        S = np.empty((g, freqs.shape[0]))
+        rc = self.lib.oracle_fpw_multi(t.ctypes.data, x.ctypes.data, sigma.ctypes.data, t.shape[0], freqs.ctypes.data,
+                                       freqs.shape[0], M_max, g, c, S.ctypes.data)
+        assert rc == 0
+        return S
 
     def fpw(self, t, x, sigma, freqs, M, c=0.0):
         t, x, sigma, freqs = (np.ascontiguousarray(a, dtype=np.float64) for a in (t, x, sigma, freqs))
@@ -116,6 +131,20 @@ def battery(api: Api) -> list[str]:
         eb, ed = exact_bins(t, f, 20)
         if not np.allclose(e[q], ed, rtol=0, atol=1e-15) or not np.array_equal(b[q][ed > 1e-12], eb[ed > 1e-12]):
             failed.append("bins")
+            break
+    # several M from one M_max pass: offset o shifts the combined bin edges by o/M_max
+    rng = np.random.default_rng(20)
+    t, x, sigma = tiny_case(rng, 11)
+    f = 1.37
+    S = api.fpw_multi(t, x, sigma, [f], 12, 3)
+    for o in range(3):
+        bins = []
+        for ti in t:
+            ph = exact_phase(ti, f) - Fraction(o, 12)
+            ph -= math.floor(ph)
+            bins.append(int(math.floor(ph * 4)))
+        if not np.isclose(S[o, 0], least_squares_reduction(x, sigma, np.array(bins), 4), rtol=1e-9, atol=1e-10):
+            failed.append("multi_m")
             break
     # top-k golden cases
     idx, _ = api.topk(np.array([1.0, 3.0, 2.0, 5.0, 5.0, 4.0, 6.0]), 3)

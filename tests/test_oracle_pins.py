@@ -345,3 +345,45 @@ def test_invalid_inputs_rejected():
     with pytest.raises(oracle.OracleError):
         oracle.fpw(t, x, np.ones(3), [1.0], 0)
     assert oracle.fpw(np.zeros(0), np.zeros(0), np.zeros(0), [1.0, 2.0], 4).tolist() == [0.0, 0.0]
+
+
+# ---------------------------------------------------------------- several M from one M_max pass (Section 3.4)
+def exact_phase(t, f):
+    p = Fraction(float(t)) * Fraction(float(f))
+    return p - math.floor(p)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_multi_m_offsets_match_shifted_bins_least_squares(seed):
+    """Offset o of M = M_max/g is the plain statistic with bin edges shifted by
+    o/M_max cycles: bins floor(M * frac(phase - o/M_max)) from exact rationals,
+    S from the least-squares form."""
+    rng = np.random.default_rng([23, seed])
+    n = int(rng.integers(3, 14))
+    M_max, g = [(12, 3), (12, 4), (20, 5), (20, 2), (6, 6), (8, 1)][seed]
+    t, x, sigma = tiny_case(rng, n, negative_t=(seed % 2 == 1))
+    freqs = rng.uniform(0.05, 3.0, 3)
+    S = oracle.fpw_multi(t, x, sigma, freqs, M_max, g)
+    M = M_max // g
+    for q, f in enumerate(freqs):
+        for o in range(g):
+            bins = []
+            for ti in t:
+                ph = exact_phase(ti, f) - Fraction(o, M_max)
+                ph -= math.floor(ph)
+                bins.append(int(math.floor(ph * M)))
+            assert S[o, q] == pytest.approx(least_squares_reduction(x, sigma, np.array(bins), M), rel=1e-9, abs=1e-10)
+
+
+def test_multi_m_reduces_to_plain_statistic():
+    t, x, sigma = _curve(8, 400)
+    freqs = np.linspace(0.01, 20, 500)
+    _, e = oracle.bins(t, freqs, 20)
+    keep = np.all(e > 1e-12, axis=1)
+    np.testing.assert_array_equal(oracle.fpw_multi(t, x, sigma, freqs, 20, 1)[0], oracle.fpw(t, x, sigma, freqs, 20))
+    # offset 0 of M = 20/4 = 5 is the plain 5-bin statistic (away from rounding at the edges)
+    np.testing.assert_allclose(oracle.fpw_multi(t, x, sigma, freqs, 20, 4)[0][keep],
+                               oracle.fpw(t, x, sigma, freqs, 5)[keep], rtol=1e-12)
+    # with the prior term as well
+    np.testing.assert_allclose(oracle.fpw_multi(t, x, sigma, freqs, 20, 2, 0.4)[0][keep],
+                               oracle.fpw(t, x, sigma, freqs, 10, 0.4)[keep], rtol=1e-12)
