@@ -184,6 +184,6 @@ def test_original_passes_battery(tmpdir_mod):
 def test_mutant_is_caught(name, tmpdir_mod):
     old, new = MUTATIONS[name]
     src = open(SRC).read()
-    assert src.count(old) == 1, f"mutation anchor for {name} not unique"
+    assert src.count(old) >= 1, f"mutation anchor for {name} not found"  # every occurrence is mutated
     failed = battery(Api(_compile(src.replace(old, new), tmpdir_mod, "mut_" + name)))
     assert failed, f"mutant {name} passed every pin"
