@@ -145,6 +145,48 @@ FPW_API int fpw_periodogram_batch_ex(fpw_ctx* ctx, void* stream, const fpw_param
                              const double* sigma, const double* freqs, int64_t nfreq, int M, int k,
                              int32_t* topk_idx, float* topk_S, double* S_out);
 
+/* Several bin counts from one pass (Section 3.4): the bin sums at M_max bins
+ * are combined into M = M_max / g bins for each requested group g, with each
+ * of the g bin offsets o (combined bin j holds the M_max-bins (j g + o + u) mod
+ * M_max, u < g; the offset shifts every bin edge by o / M_max of a cycle).
+ * For each curve and group the periodogram reported is S_g(f) = the largest S
+ * over the g offsets (ties to the lower offset), and its peaks are ranked as
+ * in fpw_periodogram_batch.
+ *   groups:      HOST int[ngroups], 1 <= ngroups <= 8, each g in [1, 64] dividing M_max
+ *   topk_idx:    device int32[ncurves * ngroups * k], row (c * ngroups + q) per curve and group
+ *   topk_offset: device int32[ncurves * ngroups * k], the offset o of each peak (-1 if none)
+ *   topk_S:      device float32[ncurves * ngroups * k]
+ *   S_out:       optional device float64[ncurves * ngroups * nfreq], S_g(f) per curve and group
+ * Other arguments as fpw_periodogram_batch_ex. FP32 sums only (FPW_ENOTSUP
+ * otherwise); nfreq < 2^25 when k > 0. Stream-ordered. */
+FPW_API int fpw_periodogram_batch_multi(fpw_ctx* ctx, void* stream, const fpw_params* params, const int64_t* offsets,
+                                        const int64_t* offsets_host, int64_t ncurves, const double* t,
+                                        const double* x, const double* sigma, const double* freqs, int64_t nfreq,
+                                        int M_max, const int* groups, int ngroups, int k, int32_t* topk_idx,
+                                        int32_t* topk_offset, float* topk_S, double* S_out);
+
+/* Phase entropy (Appendix C) of one set of observation times at every trial
+ * frequency: H(f) = -sum_m (N_m/N) log(N_m/N), N_m the observations in phase bin
+ * m (bins as the periodogram kernels assign them), natural logarithm, FP32.
+ * The paper computes it once per field (it depends on the times only) to flag
+ * periods whose phase coverage is uneven.
+ *   t: device float64[n] (finite); freqs: device float64[nfreq]; 1 <= M <= 256;
+ *   H_out: device float32[nfreq]. Stream-ordered. Errors: FPW_EINVAL, FPW_ECUDA. */
+FPW_API int fpw_phase_entropy(fpw_ctx* ctx, void* stream, const double* t, int64_t n, const double* freqs,
+                              int64_t nfreq, int M, float* H_out);
+
+/* Phase entropy at each reported peak of a batch (Appendix C, the paper's ZTF
+ * practice) and its z-score against Hutcheson's approximations for equally
+ * likely bins: E(H) = log M - (M-1)/(2N) - (M-1)(M+1)/(12N^2),
+ * Var(H) = (M-1)/(2N^2) + (M^2-1)/(6N^3), z = (H - E)/sqrt(Var).
+ *   offsets, t, freqs: as for the batch call (device); topk_idx: device
+ *   int32[ncurves * k] (e.g. fpw_periodogram_batch's output; -1 or out-of-range
+ *   entries give NaN); H_out, z_out: device float32[ncurves * k]; 1 <= M <= 4096.
+ * Stream-ordered. Errors: FPW_EINVAL, FPW_ECUDA. */
+FPW_API int fpw_phase_entropy_peaks(fpw_ctx* ctx, void* stream, const int64_t* offsets, int64_t ncurves,
+                                    const double* t, const double* freqs, int64_t nfreq, int M, int k,
+                                    const int32_t* topk_idx, float* H_out, float* z_out);
+
 /* End-to-end form with HOST buffers: copies the inputs to context-owned device
  * memory, runs fpw_periodogram_batch_ex, copies the top-k back and
  * synchronizes. All pointers are host pointers (pinned memory copies fastest).

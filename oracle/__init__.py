@@ -21,6 +21,7 @@ Functions and the passages they follow:
   post-processing).
 * :func:`fpw_multi` -- Section 3.4: S for M = M_max / g from the M_max-bin sums,
   for each of the g bin offsets.
+* :func:`phase_entropy` -- Appendix C, phase entropy of the times per frequency.
 * :func:`topk` -- the k highest local maxima of a periodogram (Section 3.5).
 * :func:`bins` -- bin of every (frequency, observation) pair and the exact
   distance from t*f to the nearest bin edge, for bin-mismatch accounting.
@@ -78,6 +79,8 @@ def _load():
             lib.oracle_bins.restype = c_int
             lib.oracle_fpw_multi.argtypes = [vp, vp, vp, i64, vp, i64, c_int, c_int, d, vp]
             lib.oracle_fpw_multi.restype = c_int
+            lib.oracle_phase_entropy.argtypes = [vp, i64, vp, i64, c_int, vp]
+            lib.oracle_phase_entropy.restype = c_int
             lib.oracle_min_edge.argtypes = [vp, i64, vp, i64, c_int, vp]
             lib.oracle_min_edge.restype = c_int
             lib.oracle_version.restype = c_int
@@ -120,6 +123,15 @@ def fpw_multi(t, x, sigma, freqs, M_max: int, g: int, inv_alpha2: float = 0.0) -
     _check(lib.oracle_fpw_multi(_ptr(t), _ptr(x), _ptr(sigma), t.shape[0], _ptr(freqs), freqs.shape[0], int(M_max),
                                 int(g), float(inv_alpha2), _ptr(S)))
     return S
+
+
+def phase_entropy(t, freqs, M: int) -> np.ndarray:
+    """Appendix C: phase entropy of the times at each frequency (natural log)."""
+    lib = _load()
+    t, freqs = _f64(t), _f64(freqs)
+    H = np.empty(freqs.shape[0], dtype=np.float64)
+    _check(lib.oracle_phase_entropy(_ptr(t), t.shape[0], _ptr(freqs), freqs.shape[0], int(M), _ptr(H)))
+    return H
 
 
 def fpw_batch(offsets, t, x, sigma, freqs, M: int, inv_alpha2: float = 0.0, *, nthreads: int | None = None,

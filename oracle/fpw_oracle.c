@@ -167,6 +167,29 @@ int oracle_fpw_multi(const double* t, const double* x, const double* sigma, int6
   return ORACLE_OK;
 }
 
+/* Appendix C, phase entropy of the observation times at each frequency:
+ * H = -sum_m (N_m / N) log(N_m / N) over the occupied bins, N_m the number of
+ * observations in bin m (Appendix A.1 bins), N the number of observations
+ * (natural logarithm; N = 0 gives 0). */
+int oracle_phase_entropy(const double* t, int64_t n, const double* freqs, int64_t nfreq, int M, double* H_out) {
+  if (n < 0 || nfreq < 0 || M < 1 || (nfreq > 0 && (!freqs || !H_out)) || (n > 0 && !t)) return ORACLE_EINVAL;
+  int64_t* cnt = (int64_t*)malloc(sizeof(int64_t) * (size_t)M);
+  if (!cnt) return ORACLE_ENOMEM;
+  for (int64_t k = 0; k < nfreq; ++k) {
+    for (int m = 0; m < M; ++m) cnt[m] = 0;
+    for (int64_t i = 0; i < n; ++i) cnt[oracle_bin(t[i], freqs[k], M)] += 1;
+    double H = 0.0;
+    for (int m = 0; m < M; ++m) {
+      if (cnt[m] == 0) continue;
+      double p = (double)cnt[m] / (double)n;
+      H -= p * log(p);
+    }
+    H_out[k] = H;
+  }
+  free(cnt);
+  return ORACLE_OK;
+}
+
 /* Peaks of a periodogram (Section 3.5 post-processing, reading above). */
 static int is_peak(const double* S, int64_t nfreq, int64_t k) {
   if (nfreq == 1) return 1;

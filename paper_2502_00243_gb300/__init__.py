@@ -29,7 +29,8 @@ FPW_MAX_TOPK = 64
 EXPORTED = ("fpw_params_default", "fpw_ctx_create", "fpw_ctx_destroy", "fpw_ctx_status", "fpw_periodogram",
             "fpw_periodogram_ex", "fpw_periodogram_batch", "fpw_periodogram_batch_ex", "fpw_periodogram_batch_host",
             "fpw_debug_bins", "fpw_strerror", "fpw_version", "fpw_last_cuda_error", "fpw_ctx_set_timing",
-            "fpw_ctx_kernel_time", "fpw_periodogram_batch_noalloc", "fpw_ctx_set_shape", "fpw_ctx_clear_shapes")
+            "fpw_ctx_kernel_time", "fpw_periodogram_batch_noalloc", "fpw_ctx_set_shape", "fpw_ctx_clear_shapes",
+            "fpw_periodogram_batch_multi", "fpw_phase_entropy", "fpw_phase_entropy_peaks")
 
 
 class FPWError(RuntimeError):
@@ -86,6 +87,10 @@ def lib():
                 "fpw_periodogram_batch_noalloc": (ci, [vp, P, vp, vp, i64, vp, vp, vp, vp, i64, ci, ci, vp, vp]),
                 "fpw_ctx_set_shape": (ci, [vp, ci, ci, i64, i64, ci, ci, ci]),
                 "fpw_ctx_clear_shapes": (ci, [vp]),
+                "fpw_phase_entropy": (ci, [vp, vp, vp, i64, vp, i64, ci, vp]),
+                "fpw_phase_entropy_peaks": (ci, [vp, vp, vp, i64, vp, vp, i64, ci, ci, vp, vp, vp]),
+                "fpw_periodogram_batch_multi": (ci, [vp, vp, P, vp, vp, i64, vp, vp, vp, vp, i64, ci, vp, ci, ci, vp, vp,
+                                                     vp, vp]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -258,6 +263,49 @@ def fpw_periodogram_batch_ex(ctx: Context, stream, params, offsets, offsets_host
         _dev(S_out, torch.float64, "S_out") if S_out is not None else None)
     _check(rc, "fpw_periodogram_batch_ex")
     return topk_idx, topk_S, S_out
+
+
+def fpw_periodogram_batch_multi(ctx: Context, stream, params, offsets, offsets_host, t, x, sigma, freqs, M_max: int,
+                                groups, k: int, topk_idx, topk_offset, topk_S, S_out=None):
+    """Several M = M_max / g from one M_max pass (Section 3.4); see include/fpw.h."""
+    import torch
+    g = np.ascontiguousarray(groups, dtype=np.int32)
+    oh = None
+    if offsets_host is not None:
+        offsets_host = np.ascontiguousarray(offsets_host, dtype=np.int64)
+        oh = ctypes.c_void_p(offsets_host.ctypes.data)
+    rc = lib().fpw_periodogram_batch_multi(
+        ctx.handle, _stream(stream), _params(params), _dev(offsets, torch.int64, "offsets"), oh, offsets.numel() - 1,
+        _dev(t, torch.float64, "t"), _dev(x, torch.float64, "x"), _dev(sigma, torch.float64, "sigma"),
+        _dev(freqs, torch.float64, "freqs"), freqs.numel(), int(M_max), ctypes.c_void_p(g.ctypes.data), int(g.size),
+        int(k), _dev(topk_idx, torch.int32, "topk_idx") if topk_idx is not None else None,
+        _dev(topk_offset, torch.int32, "topk_offset") if topk_offset is not None else None,
+        _dev(topk_S, torch.float32, "topk_S") if topk_S is not None else None,
+        _dev(S_out, torch.float64, "S_out") if S_out is not None else None)
+    _check(rc, "fpw_periodogram_batch_multi")
+    return topk_idx, topk_offset, topk_S, S_out
+
+
+def fpw_phase_entropy(ctx: Context, stream, t, freqs, M: int, H_out):
+    """Appendix C phase entropy of one set of times at every frequency."""
+    import torch
+    rc = lib().fpw_phase_entropy(ctx.handle, _stream(stream), _dev(t, torch.float64, "t"), t.numel(),
+                                 _dev(freqs, torch.float64, "freqs"), freqs.numel(), int(M),
+                                 _dev(H_out, torch.float32, "H_out"))
+    _check(rc, "fpw_phase_entropy")
+    return H_out
+
+
+def fpw_phase_entropy_peaks(ctx: Context, stream, offsets, t, freqs, M: int, k: int, topk_idx, H_out, z_out):
+    """Phase entropy and its Hutcheson z-score at each reported peak."""
+    import torch
+    rc = lib().fpw_phase_entropy_peaks(ctx.handle, _stream(stream), _dev(offsets, torch.int64, "offsets"),
+                                       offsets.numel() - 1, _dev(t, torch.float64, "t"),
+                                       _dev(freqs, torch.float64, "freqs"), freqs.numel(), int(M), int(k),
+                                       _dev(topk_idx, torch.int32, "topk_idx"), _dev(H_out, torch.float32, "H_out"),
+                                       _dev(z_out, torch.float32, "z_out"))
+    _check(rc, "fpw_phase_entropy_peaks")
+    return H_out, z_out
 
 
 def _host(a, dtype, name):

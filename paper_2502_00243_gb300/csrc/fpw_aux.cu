@@ -71,13 +71,16 @@ __global__ void merge_kernel(const MergeArgs a) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   const bool grid_bad = (*a.status & kStatusGrid) != 0u;
+  const int64_t stride = a.out_stride > 0 ? a.out_stride : a.k;
   for (int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < a.ncurves; c += warps) {
-    int32_t* oi = a.topk_idx + c * a.k;
-    float* os = a.topk_S + c * a.k;
+    int32_t* oi = a.topk_idx + c * stride;
+    float* os = a.topk_S + c * stride;
+    int32_t* oo = a.topk_off ? a.topk_off + c * stride : nullptr;
     if (grid_bad || a.curve_bad[c]) {
       for (int q = lane; q < a.k; q += 32) {
         oi[q] = -1;
         os[q] = __int_as_float(0x7fc00000);
+        if (oo) oo[q] = -1;
       }
       continue;
     }
@@ -100,13 +103,19 @@ __global__ void merge_kernel(const MergeArgs a) {
       }
       warp_best(bs, bi, bp);
       if (lane == 0) {
-        oi[q] = (bp >= 0) ? bi : -1;
+        if (oo) {
+          oi[q] = (bp >= 0) ? (bi >> 6) : -1;
+          oo[q] = (bp >= 0) ? (bi & 63) : -1;
+        } else {
+          oi[q] = (bp >= 0) ? bi : -1;
+        }
         os[q] = (bp >= 0) ? (float)bs : __int_as_float(0x7fc00000);
       }
       if (bp < 0) {
         for (int r = q + 1 + lane; r < a.k; r += 32) {
           oi[r] = -1;
           os[r] = __int_as_float(0x7fc00000);
+          if (oo) oo[r] = -1;
         }
         break;
       }

@@ -19,6 +19,9 @@ constexpr unsigned kStatusTimeout = 4u;  // a bounded wait gave up
 // evaluated with a direct per-frequency anchor instead.
 constexpr double kGridTolCycles = 2e-10;
 
+// Largest number of derived bin counts computed from one M_max pass.
+constexpr int kMaxGroups = 8;
+
 // One unit of persistent work: frequencies [f_lo, f_hi) of curve `curve`.
 // Its top-k candidates go to row `slot` of the candidate table.
 struct WorkItem {
@@ -50,6 +53,9 @@ struct TileArgs {
   int obs_chunk;             // observations staged per pass
   double inv_alpha2;
   const double* tile_dev;    // per-tile grid deviation (tile_dev_kernel), or NULL: checked in the tile kernel
+  int ngroups;               // several-M kernel: number of groups (0 = the single-M kernel)
+  int group_g[kMaxGroups];   // M = M / group_g[q] for group q
+  int64_t group_rows;        // candidate rows per group (cand tables are [group][slot][k])
 };
 
 struct PrepArgs {
@@ -75,8 +81,10 @@ struct MergeArgs {
   const unsigned* status;
   int64_t ncurves;
   int k;
-  int32_t* topk_idx;
+  int32_t* topk_idx;         // curve c's list starts at c * out_stride (out_stride = k when 0)
   float* topk_S;
+  int out_stride;
+  int32_t* topk_off;         // several-M: receives key & 63 (the bin offset); topk_idx then gets key >> 6
 };
 
 struct PlainArgs {           // binary64 plain form, one curve
@@ -122,8 +130,8 @@ struct TileShape {
 };
 
 // ---- launch wrappers (defined in the .cu files) -------------------------
-size_t tile_smem_bytes(int T, int R, int M, int NC, int k, bool accum64);
-int tile_max_blocks_per_sm(int R, int phase_mode, bool accum64, int T, size_t smem);
+size_t tile_smem_bytes(int T, int R, int M, int NC, int k, bool accum64, int ngroups = 0);
+int tile_max_blocks_per_sm(int R, int phase_mode, bool accum64, int T, size_t smem, bool multi = false);
 bool tile_supported_R(int R);
 cudaError_t launch_tile(const TileArgs& a, const TileShape& s, int phase_mode, bool accum64, int grid,
                         cudaStream_t st);
@@ -139,6 +147,11 @@ cudaError_t launch_fill_topk(int32_t* idx, float* S, int64_t n, cudaStream_t st)
 cudaError_t tile_init_attributes(int max_smem);
 cudaError_t plain_init_attributes(int max_smem);
 size_t plain_smem_bytes(int M);
+cudaError_t launch_entropy_dense(const double* t, int64_t n, const double* freqs, int64_t nfreq, int M, float* H_out,
+                                 cudaStream_t st);
+cudaError_t launch_entropy_peaks(const int64_t* offsets, int64_t ncurves, const double* t, const double* freqs,
+                                 int64_t nfreq, int M, int k, const int32_t* topk_idx, float* H_out, float* z_out,
+                                 cudaStream_t st);
 
 // ---- device arithmetic --------------------------------------------------
 #ifdef __CUDACC__

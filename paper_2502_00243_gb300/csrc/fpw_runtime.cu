@@ -175,7 +175,8 @@ bool valid_params(const fpw_params& p) {
 // beyond, T = 128 (halved while the bins alone do not fit). NC: the largest
 // chunk that keeps two resident blocks per SM (one stages while the other
 // accumulates), else one block per SM.
-int choose_shape(fpw_ctx* ctx, const fpw_params& p, int M, int k, int64_t max_n, int64_t n_typ, TileShape& out) {
+int choose_shape(fpw_ctx* ctx, const fpw_params& p, int M, int k, int64_t max_n, int64_t n_typ, int ngroups,
+                 TileShape& out) {
   const bool acc64 = p.accum == FPW_ACCUM_FP64;
   int T = 128, R = 4, NC = 0;
   if (acc64)
@@ -198,11 +199,11 @@ int choose_shape(fpw_ctx* ctx, const fpw_params& p, int M, int k, int64_t max_n,
   if (p.freqs_per_thread) R = p.freqs_per_thread;
   if (p.obs_chunk) NC = p.obs_chunk;
   const bool fixedT = p.threads != 0;
-  while (!fixedT && T > 32 && tile_smem_bytes(T, R, M, 32, k, acc64) > (size_t)ctx->smem_optin) T /= 2;
+  while (!fixedT && T > 32 && tile_smem_bytes(T, R, M, 32, k, acc64, ngroups) > (size_t)ctx->smem_optin) T /= 2;
   const int64_t want_nc = std::max<int64_t>(32, ((max_n + 31) / 32) * 32);
   const size_t per_sm = (size_t)ctx->smem_per_sm;
   auto fits = [&](int blocks, int nc) {
-    const size_t s = tile_smem_bytes(T, R, M, nc, k, acc64);
+    const size_t s = tile_smem_bytes(T, R, M, nc, k, acc64, ngroups);
     return s <= (size_t)ctx->smem_optin && (s + 1024) * blocks <= per_sm;
   };
   if (!NC) {
@@ -224,7 +225,7 @@ int choose_shape(fpw_ctx* ctx, const fpw_params& p, int M, int k, int64_t max_n,
     }
     if (!NC) return FPW_ENOTSUP;  // the bins alone exceed shared memory
   }
-  const size_t smem = tile_smem_bytes(T, R, M, NC, k, acc64);
+  const size_t smem = tile_smem_bytes(T, R, M, NC, k, acc64, ngroups);
   if (smem > (size_t)ctx->smem_optin) return FPW_ENOTSUP;
   out.threads = T;
   out.R = R;
@@ -352,6 +353,9 @@ struct BatchCall {
   int32_t* topk_idx;
   float* topk_S;
   double* S_out;
+  int ngroups;              // several-M call: groups g (M = M_max / g); 0 = single M
+  int groups[kMaxGroups];
+  int32_t* topk_off;        // several-M call: offset of each reported peak
 };
 
 void drop_graphs(fpw_ctx* ctx) {
@@ -404,6 +408,9 @@ int enqueue_tile_path(fpw_ctx* ctx, const BatchCall& b, Plan* pl, unsigned* word
   ta.obs_chunk = pl->shape.obs_chunk;
   ta.inv_alpha2 = b.p.inv_alpha2;
   ta.tile_dev = static_cast<const double*>(ctx->tile_dev.p);
+  ta.ngroups = b.ngroups;
+  for (int q = 0; q < b.ngroups; ++q) ta.group_g[q] = b.groups[q];
+  ta.group_rows = pl->nslots;
   const bool timed = ctx->timing && !b.p.use_graph;
   if (timed) {
     while (ctx->ev.size() < ctx->ev_used + 2) {
@@ -419,17 +426,23 @@ int enqueue_tile_path(fpw_ctx* ctx, const BatchCall& b, Plan* pl, unsigned* word
     ctx->ev_used += 2;
   }
   if (b.k > 0) {
-    MergeArgs ma{};
-    ma.cand_S = static_cast<const double*>(ctx->cand_S.p);
-    ma.cand_idx = static_cast<const int32_t*>(ctx->cand_idx.p);
-    ma.cand_base = static_cast<const int32_t*>(pl->cand_base.p);
-    ma.curve_bad = static_cast<const uint8_t*>(ctx->curve_bad.p);
-    ma.status = words + 1;
-    ma.ncurves = b.C;
-    ma.k = b.k;
-    ma.topk_idx = b.topk_idx;
-    ma.topk_S = b.topk_S;
-    FPW_CK(launch_merge(ma, st));
+    const int ng = b.ngroups > 0 ? b.ngroups : 1;
+    for (int q = 0; q < ng; ++q) {
+      const int64_t rows = (int64_t)q * pl->nslots * b.k;
+      MergeArgs ma{};
+      ma.cand_S = static_cast<const double*>(ctx->cand_S.p) + rows;
+      ma.cand_idx = static_cast<const int32_t*>(ctx->cand_idx.p) + rows;
+      ma.cand_base = static_cast<const int32_t*>(pl->cand_base.p);
+      ma.curve_bad = static_cast<const uint8_t*>(ctx->curve_bad.p);
+      ma.status = words + 1;
+      ma.ncurves = b.C;
+      ma.k = b.k;
+      ma.topk_idx = b.topk_idx + (int64_t)q * b.k;
+      ma.topk_S = b.topk_S + (int64_t)q * b.k;
+      ma.out_stride = ng * b.k;
+      ma.topk_off = b.ngroups > 0 ? b.topk_off + (int64_t)q * b.k : nullptr;
+      FPW_CK(launch_merge(ma, st));
+    }
   }
   FPW_CK(launch_latch(words, st));
   return FPW_OK;
@@ -447,9 +460,9 @@ int run_tile_path(fpw_ctx* ctx, const BatchCall& b) {
   }
   const int64_t n_typ = sn > 0.0 ? (int64_t)(sn2 / sn) : 0;  // observation-weighted mean curve size
   TileShape sh{};
-  int rc = choose_shape(ctx, b.p, b.M, b.k, max_n, n_typ, sh);
+  int rc = choose_shape(ctx, b.p, b.M, b.k, max_n, n_typ, b.ngroups, sh);
   if (rc != FPW_OK) return rc;
-  const int bps = tile_max_blocks_per_sm(sh.R, b.p.phase_mode, acc64, sh.threads, sh.smem);
+  const int bps = tile_max_blocks_per_sm(sh.R, b.p.phase_mode, acc64, sh.threads, sh.smem, b.ngroups > 0);
   if (bps < 1) return FPW_ENOTSUP;
   Plan* pl = get_plan(ctx, b.off_h, b.C, b.F, sh, bps, &rc);
   if (!pl) return rc;
@@ -461,8 +474,9 @@ int run_tile_path(fpw_ctx* ctx, const BatchCall& b) {
     const int64_t Wown = (int64_t)sh.threads * sh.R - 2;
     if (e == cudaSuccess) e = ensure(ctx->tile_dev, sizeof(double) * (size_t)((b.F + Wown - 1) / Wown + 1));
   }
-  if (e == cudaSuccess && b.k > 0) e = ensure(ctx->cand_S, (size_t)pl->nslots * b.k * sizeof(double));
-  if (e == cudaSuccess && b.k > 0) e = ensure(ctx->cand_idx, (size_t)pl->nslots * b.k * sizeof(int32_t));
+  const size_t ng = (size_t)(b.ngroups > 0 ? b.ngroups : 1);
+  if (e == cudaSuccess && b.k > 0) e = ensure(ctx->cand_S, ng * pl->nslots * b.k * sizeof(double));
+  if (e == cudaSuccess && b.k > 0) e = ensure(ctx->cand_idx, ng * pl->nslots * b.k * sizeof(int32_t));
   if (e == cudaSuccess) e = ensure(ctx->curve_bad, (size_t)b.C + 16);
   if (e != cudaSuccess) return cuda_fail(e, "scratch allocation");
   void* after[6] = {ctx->aw.p, ctx->cand_S.p, ctx->cand_idx.p, ctx->curve_bad.p, ctx->words.p, ctx->tile_dev.p};
@@ -484,6 +498,9 @@ int run_tile_path(fpw_ctx* ctx, const BatchCall& b) {
   gk = mix(gk, b.p.accum);
   gk = mix(gk, b.p.K);
   gk = mix(gk, b.p.peak_mode);
+  gk = mix(gk, b.ngroups);
+  for (int q = 0; q < b.ngroups; ++q) gk = mix(gk, b.groups[q]);
+  gk = mix(gk, (const void*)b.topk_off);
   gk = mix(gk, ctx->aw.p);
   gk = mix(gk, ctx->cand_S.p);
   gk = mix(gk, ctx->cand_idx.p);
@@ -805,6 +822,71 @@ int fpw_periodogram_batch_ex(fpw_ctx* ctx, void* stream, const fpw_params* param
   return batch_impl(ctx, b);
 }
 
+int fpw_periodogram_batch_multi(fpw_ctx* ctx, void* stream, const fpw_params* params, const int64_t* offsets,
+                                const int64_t* offsets_host, int64_t ncurves, const double* t, const double* x,
+                                const double* sigma, const double* freqs, int64_t nfreq, int M_max, const int* groups,
+                                int ngroups, int k, int32_t* topk_idx, int32_t* topk_offset, float* topk_S,
+                                double* S_out) {
+  if (!ctx || ncurves < 0 || nfreq < 0 || M_max < 1 || k < 0 || k > FPW_MAX_TOPK) return FPW_EINVAL;
+  if (!groups || ngroups < 1 || ngroups > kMaxGroups) return FPW_EINVAL;
+  for (int q = 0; q < ngroups; ++q)
+    if (groups[q] < 1 || groups[q] > 64 || M_max % groups[q] != 0) return FPW_EINVAL;
+  if (k > 0 && nfreq >= ((int64_t)1 << 25)) return FPW_EINVAL;  // ranking key (k << 6) | offset must fit 31 bits
+  if (ncurves > 0 && !offsets) return FPW_EINVAL;
+  if (ncurves > 0 && nfreq > 0 && !freqs) return FPW_EINVAL;
+  if (ncurves > 0 && k > 0 && (!topk_idx || !topk_S || !topk_offset)) return FPW_EINVAL;
+  fpw_params p;
+  fpw_params_default(&p);
+  if (params) p = *params;
+  if (!valid_params(p)) return FPW_EINVAL;
+  if (p.accum != FPW_ACCUM_FP32 || p.phase_mode == FPW_PHASE_FP64) return FPW_ENOTSUP;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return FPW_ECUDA;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  clear_stale_error();
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  ctx->last_stream = st;
+  if (ncurves == 0) return FPW_OK;
+  const int64_t* off_h = offsets_host;
+  if (!off_h) {
+    ctx->off_host.resize((size_t)ncurves + 1);
+    FPW_CK(cudaMemcpyAsync(ctx->off_host.data(), offsets, sizeof(int64_t) * (size_t)(ncurves + 1),
+                           cudaMemcpyDeviceToHost, st));
+    FPW_CK(cudaStreamSynchronize(st));
+    off_h = ctx->off_host.data();
+  }
+  if (check_offsets(off_h, ncurves) != FPW_OK) return FPW_EINVAL;
+  if (off_h[ncurves] > 0 && (!t || !x || !sigma)) return FPW_EINVAL;
+  BatchCall b{};
+  b.stream = st;
+  b.p = p;
+  b.offsets = offsets;
+  b.off_h = off_h;
+  b.C = ncurves;
+  b.t = t;
+  b.x = x;
+  b.sigma = sigma;
+  b.freqs = freqs;
+  b.F = nfreq;
+  b.M = M_max;
+  b.k = k;
+  b.topk_idx = topk_idx;
+  b.topk_S = topk_S;
+  b.S_out = S_out;
+  b.ngroups = ngroups;
+  for (int q = 0; q < ngroups; ++q) b.groups[q] = groups[q];
+  b.topk_off = topk_offset;
+  if (nfreq == 0) {
+    if (k > 0) {
+      FPW_CK(launch_fill_topk(topk_idx, topk_S, ncurves * ngroups * k, st));
+      FPW_CK(launch_fill_topk(topk_offset, topk_S, ncurves * ngroups * k, st));
+    }
+    return FPW_OK;
+  }
+  if (nfreq > ((int64_t)1 << 31) - 1024 || ncurves > ((int64_t)1 << 31) - 1) return FPW_EINVAL;
+  return run_tile_path(ctx, b);
+}
+
 int fpw_periodogram_batch(const int64_t* offsets, int64_t ncurves, const double* t, const double* x,
                           const double* sigma, const double* freqs, int64_t nfreq, int M, int k, int32_t* topk_idx,
                           float* topk_S) {
@@ -943,6 +1025,36 @@ int fpw_periodogram_batch_host(fpw_ctx* ctx, const fpw_params* params, const int
     FPW_CK(cudaMemcpyAsync(topk_S, ctx->h_S.p, sizeof(float) * (size_t)(ncurves * k), cudaMemcpyDeviceToHost, st));
   }
   return sync_status(ctx, st, FPW_OK);
+}
+
+int fpw_phase_entropy(fpw_ctx* ctx, void* stream, const double* t, int64_t n, const double* freqs, int64_t nfreq,
+                      int M, float* H_out) {
+  if (!ctx || n < 0 || nfreq < 0 || M < 1 || M > 256) return FPW_EINVAL;
+  if (nfreq > 0 && (!freqs || !H_out)) return FPW_EINVAL;
+  if (n > 0 && !t) return FPW_EINVAL;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return FPW_ECUDA;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  clear_stale_error();
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  ctx->last_stream = st;
+  FPW_CK(launch_entropy_dense(t, n, freqs, nfreq, M, H_out, st));
+  return FPW_OK;
+}
+
+int fpw_phase_entropy_peaks(fpw_ctx* ctx, void* stream, const int64_t* offsets, int64_t ncurves, const double* t,
+                            const double* freqs, int64_t nfreq, int M, int k, const int32_t* topk_idx, float* H_out,
+                            float* z_out) {
+  if (!ctx || ncurves < 0 || nfreq < 0 || M < 1 || M > 4096 || k < 0) return FPW_EINVAL;
+  if (ncurves > 0 && k > 0 && (!offsets || !freqs || !topk_idx || !H_out || !z_out || !t)) return FPW_EINVAL;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return FPW_ECUDA;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  clear_stale_error();
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  ctx->last_stream = st;
+  FPW_CK(launch_entropy_peaks(offsets, ncurves, t, freqs, nfreq, M, k, topk_idx, H_out, z_out, st));
+  return FPW_OK;
 }
 
 int fpw_debug_bins(fpw_ctx* ctx, void* stream, const fpw_params* params, const double* t, int64_t n,

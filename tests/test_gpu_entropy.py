@@ -1,0 +1,77 @@
+"""Phase entropy (Appendix C) on the GPU against the oracle: the dense entropy
+periodogram of one set of times, and entropy plus Hutcheson z-score at the
+peaks reported by the batched call."""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import pytest
+
+import lightcurves as L
+import oracle
+from gpu_util import run_batch, to_dev
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2502_00243_gb300 as G_
+    return G_
+
+
+@pytest.mark.parametrize("M", [4, 20, 50])
+def test_dense_phase_entropy(G, M):
+    w = L.make("single_ztf", nfreq=40_000)
+    t, _, _ = w.curve(0)
+    ctx = G.Context(0)
+    H = torch.empty(w.nfreq, dtype=torch.float32, device="cuda")
+    G.fpw_phase_entropy(ctx, None, torch.from_numpy(t).cuda(), torch.from_numpy(w.freqs).cuda(), M, H)
+    torch.cuda.synchronize()
+    H = H.cpu().numpy().astype(np.float64)
+    H_or = oracle.phase_entropy(t, w.freqs, M)
+    near = oracle.min_edge(t, w.freqs, M) <= 1e-9
+    err = np.abs(H - H_or)[~near]
+    assert err.max() < 2e-5, err.max()
+    ctx.close()
+
+
+def test_entropy_at_batch_peaks(G):
+    w = L.ragged(80, [300, 1500, 60, 900], 6000, M=20, k=5)
+    ctx = G.Context(0)
+    idx, Sk, _, st = run_batch(ctx, w)
+    assert st == 0
+    d = to_dev(w)
+    k = 5
+    H = torch.empty(w.ncurves * k, dtype=torch.float32, device="cuda")
+    z = torch.empty(w.ncurves * k, dtype=torch.float32, device="cuda")
+    ti = torch.from_numpy(idx.reshape(-1).copy()).cuda()
+    G.fpw_phase_entropy_peaks(ctx, None, d["offsets"], d["t"], d["freqs"], 20, k, ti, H, z)
+    torch.cuda.synchronize()
+    H = H.cpu().numpy().reshape(w.ncurves, k)
+    z = z.cpu().numpy().reshape(w.ncurves, k)
+    for c in range(w.ncurves):
+        t, _, _ = w.curve(c)
+        N = t.size
+        E = math.log(20) - 19 / (2 * N) - 19 * 21 / (12 * N * N)
+        V = 19 / (2 * N * N) + 399 / (6 * N ** 3)
+        for j in range(k):
+            if idx[c, j] < 0:
+                assert np.isnan(H[c, j]) and np.isnan(z[c, j])
+                continue
+            f = w.freqs[idx[c, j]]
+            h = oracle.phase_entropy(t, [f], 20)[0]
+            if oracle.min_edge(t, [f], 20)[0] > 1e-9:
+                assert abs(H[c, j] - h) < 2e-5
+                assert abs(z[c, j] - (h - E) / math.sqrt(V)) < 2e-5 / math.sqrt(V) + 1e-3
+    # an invalid index gives NaN
+    bad = torch.tensor([-1, w.nfreq + 5] + [0] * (w.ncurves * k - 2), dtype=torch.int32, device="cuda")
+    G.fpw_phase_entropy_peaks(ctx, None, d["offsets"], d["t"], d["freqs"], 20, k, bad, H_ := torch.empty_like(
+        torch.from_numpy(H.reshape(-1)).cuda()), z_ := torch.empty_like(H_))
+    torch.cuda.synchronize()
+    assert torch.isnan(H_[:2]).all() and torch.isnan(z_[:2]).all()
+    ctx.close()

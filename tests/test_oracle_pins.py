@@ -387,3 +387,46 @@ def test_multi_m_reduces_to_plain_statistic():
     # with the prior term as well
     np.testing.assert_allclose(oracle.fpw_multi(t, x, sigma, freqs, 20, 2, 0.4)[0][keep],
                                oracle.fpw(t, x, sigma, freqs, 10, 0.4)[keep], rtol=1e-12)
+
+
+# ---------------------------------------------------------------- phase entropy (Appendix C)
+def hutcheson(M, N):
+    """Appendix C: expectation and variance of the phase entropy for equal bin
+    probabilities, to the orders the paper gives."""
+    E = math.log(M) - (M - 1) / (2 * N) - (M - 1) * (M + 1) / (12 * N * N)
+    V = (M - 1) / (2 * N * N) + (M * M - 1) / (6 * N ** 3)
+    return E, V
+
+
+def test_phase_entropy_closed_forms():
+    M, per = 8, 5
+    N = M * per
+    # phases i/N at f = 1: exactly `per` observations per bin -> H = log M
+    t = np.arange(N) / N
+    assert oracle.phase_entropy(t, [1.0], M)[0] == pytest.approx(math.log(M), rel=1e-15)
+    # every observation in one bin -> H = 0 (f = 0, or integer times at integer f)
+    assert oracle.phase_entropy(t, [0.0], M)[0] == 0.0
+    assert oracle.phase_entropy(np.arange(30.0), [3.0], M)[0] == 0.0
+    # two equally filled bins -> log 2; a 1:3 split -> -(1/4 log 1/4 + 3/4 log 3/4)
+    assert oracle.phase_entropy(np.array([0.0, 0.5]), [1.0], 2)[0] == pytest.approx(math.log(2))
+    h = oracle.phase_entropy(np.array([0.1, 0.6, 0.7, 0.8]), [1.0], 2)[0]
+    assert h == pytest.approx(-(0.25 * math.log(0.25) + 0.75 * math.log(0.75)))
+    assert oracle.phase_entropy(np.zeros(0), [1.0], M)[0] == 0.0
+
+
+def test_phase_entropy_matches_hutcheson_for_random_times():
+    M, N, C = 10, 200, 400
+    rng = np.random.default_rng(31)
+    vals = [oracle.phase_entropy(rng.uniform(0, 1000, N), [rng.uniform(1.0, 5.0)], M)[0] for _ in range(C)]
+    E, V = hutcheson(M, N)
+    vals = np.array(vals)
+    assert abs(vals.mean() - E) < 5 * math.sqrt(V / C)
+    assert abs(vals.var() / V - 1.0) < 0.3
+
+
+def test_phase_entropy_ignores_order_and_fluxes():
+    t, x, sigma = _curve(9, 300)
+    f = np.linspace(0.05, 5, 200)
+    H = oracle.phase_entropy(t, f, 20)
+    np.testing.assert_allclose(oracle.phase_entropy(t[::-1].copy(), f, 20), H, rtol=1e-13)
+    assert np.all(H >= 0) and np.all(H <= math.log(20) + 1e-12)
