@@ -41,6 +41,12 @@ NSM_NOMINAL = 152
 SM_MAX_MHZ_NOMINAL = 2070.0
 SMEM_EVALS_PER_CLK_SM = 8  # 16 B (A, B) read-modify-write per evaluation at 128 B/clk/SM
 KERNELS_PER_STEP = 5  # prep, tile_dev, tile, merge, latch
+# DRAM bytes (read + write) of one tile-kernel launch, from the ncu capture summarised in
+# profiles/tile_kernel_sweep_m20_m50_full.md (1e4 sweep curves, 2e4 frequencies): 142.6 MB. The kernel
+# reads each curve from DRAM once per launch (t and the staged weights, about 16.7 B per observation;
+# per-tile re-reads hit L2), so a full launch adds only the larger grid (8 B per extra frequency).
+# Valid only for the kernel source it was measured on (sha256 prefix of fpw_tile.cu + fpw_internal.cuh).
+TILE_TRAFFIC = {"source_sha256_16": "d18ef659d00a17c4", "bytes": 142.59e6, "nfreq": 20_000}
 
 
 # ---------------------------------------------------------------- workload generation (spawned workers)
@@ -188,6 +194,23 @@ def sm_max_mhz():
             return float(json.load(fh).get("sm_max_mhz", SM_MAX_MHZ_NOMINAL))
     except (OSError, ValueError):
         return SM_MAX_MHZ_NOMINAL
+
+
+def tile_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("fpw_tile.cu", "fpw_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2502_00243_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def tile_traffic(nfreq):
+    """DRAM bytes per tile-kernel launch of the timed workload, or None when the
+    kernel source changed since the counters were taken."""
+    if tile_source_hash() != TILE_TRAFFIC["source_sha256_16"]:
+        return None
+    return TILE_TRAFFIC["bytes"] + 8.0 * (nfreq - TILE_TRAFFIC["nfreq"])
 
 
 def grid(args):
@@ -470,7 +493,7 @@ def run_gb300(args):
         peak = nsm * sm_max_mhz() * 1e6 * SMEM_EVALS_PER_CLK_SM / 1e9
         achieved = evals / (kern_ms / 1e3) / 1e9 if kern_ms > 0 else None
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Geval/s",
-                "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "frac": (achieved / peak) if achieved else None, "traffic": tile_traffic(F),
                 "kernel": "tile_kernel<R=4, fixed64, f32>", "launches": launches,
                 "kernel_ms_avg": kern_ms / max(launches, 1),
                 "peak_basis": f"shared-memory pipe: one 8 B load + one 8 B store of the (A,B) bin pair per "
@@ -487,6 +510,60 @@ def run_gb300(args):
     ctx.close()
     if dist:
         dist.destroy_process_group()
+    return 0
+
+
+# ---------------------------------------------------------------- per-workload report
+def run_configs(args):
+    """One JSON line per workload: device-resident evaluations/s of the batched
+    fixed64 path (tile-kernel time and whole-call time), and the plain binary64
+    form where it is cheap enough to time."""
+    import numpy as np
+    import torch
+
+    import lightcurves as L
+    import paper_2502_00243_gb300 as G
+    torch.cuda.set_device(0)
+    ctx = G.Context(0)
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    peak = nsm * sm_max_mhz() * 1e6 * SMEM_EVALS_PER_CLK_SM
+
+    def timed(w, M, k, params, reps=3):
+        d = [torch.from_numpy(a).cuda() for a in (w.offsets, w.t, w.x, w.sigma, w.freqs)]
+        C = w.ncurves
+        idx = torch.empty(max(C * k, 1), dtype=torch.int32, device="cuda")
+        S = torch.empty(max(C * k, 1), dtype=torch.float32, device="cuda")
+        call = lambda: G.fpw_periodogram_batch_ex(ctx, None, params, d[0], w.offsets, d[1], d[2], d[3], d[4], M, k,
+                                                  idx if k else None, S if k else None)
+        call()
+        torch.cuda.synchronize()
+        ctx.set_timing(True)
+        ctx.kernel_time()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            call()
+        e1.record()
+        torch.cuda.synchronize()
+        kms, n = ctx.kernel_time()
+        ctx.set_timing(False)
+        ev = float(w.offsets[-1]) * w.nfreq
+        return ev / (e0.elapsed_time(e1) / reps / 1e3), ev / (kms / max(n, 1) / 1e3), e0.elapsed_time(e1) / reps
+
+    cases = [("single_plain", L.make("single_plain"), 10), ("single_ztf", L.make("single_ztf"), 20),
+             ("ragged_10k", L.make("ragged_10k"), 20), ("precision", L.make("precision", range(20)), 20)]
+    for M in (10, 20, 50):
+        cases.append((f"sweep_100k/M={M} (batch of 1e4 curves)", L.make("sweep_100k", range(10_000), M=M), M))
+    for name, w, M in cases:
+        call_rate, kern_rate, ms = timed(w, M, w.k, G.fpw_params_default())
+        line = {"config": name, "curves": w.ncurves, "nobs": int(w.offsets[-1]), "nfreq": w.nfreq, "M": M,
+                "evals": float(w.offsets[-1]) * w.nfreq, "ms_per_call": ms, "evals_per_s_call": call_rate,
+                "evals_per_s_tile_kernel": kern_rate, "roofline_frac": kern_rate / peak}
+        if w.evals() <= 2e10:
+            pr, _, _ = timed(w, M, w.k, G.fpw_params_default(phase_mode=G.FPW_PHASE_FP64), reps=1)
+            line["plain_fp64_evals_per_s"] = pr
+        print(json.dumps(line), flush=True)
+    ctx.close()
     return 0
 
 
@@ -510,11 +587,14 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--autotune", action="store_true", help="measure and install tuned kernel shapes before timing")
+    ap.add_argument("--configs", action="store_true", help="report every workload (one JSON line each) instead")
     args = ap.parse_args(argv)
     if args.warmup < 0 or args.steps < 1:
         ap.error("need --steps >= 1 and --warmup >= 0")
     if args.impl == "reference":
         return run_reference(args)
+    if args.configs:
+        return run_configs(args)
     return run_gb300(args)
 
 

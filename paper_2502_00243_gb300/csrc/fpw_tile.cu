@@ -272,13 +272,12 @@ __device__ __forceinline__ void accumulate_tile(const TileArgs& args, const Bloc
         const int in = (i + 1 < cnt) ? i + 1 : i;
         const ulonglong2 pdn = sPD[in];
         const A2 awn = sAW[in];
-        unsigned long long phi = pd.x + (unsigned long long)j0 * pd.y;
+        // the R phases are independent multiply-adds (no serial chain of 64-bit adds)
+        const unsigned long long phi0 = pd.x + (unsigned long long)j0 * pd.y;
         unsigned off[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-          off[r] = bin_of_phase(phi, M) * T8 + (unsigned)r * MT8;
-          phi += pd.y;
-        }
+        for (int r = 0; r < R; ++r)
+          off[r] = bin_of_phase(phi0 + (unsigned long long)r * pd.y, M) * T8 + (unsigned)r * MT8;
         A2 v[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) v[r] = *reinterpret_cast<const A2*>(my_bins + off[r]);
