@@ -42,11 +42,11 @@ SM_MAX_MHZ_NOMINAL = 2070.0
 SMEM_EVALS_PER_CLK_SM = 8  # 16 B (A, B) read-modify-write per evaluation at 128 B/clk/SM
 KERNELS_PER_STEP = 5  # prep, tile_dev, tile, merge, latch
 # DRAM bytes (read + write) of one tile-kernel launch, from the ncu capture summarised in
-# profiles/tile_kernel_sweep_m20_m50_full.md (1e4 sweep curves, 2e4 frequencies): 142.6 MB. The kernel
+# profiles/tile_kernel_sweep_m20_m50_full.md (1e4 sweep curves, 2e4 frequencies): 143.2 MB. The kernel
 # reads each curve from DRAM once per launch (t and the staged weights, about 16.7 B per observation;
 # per-tile re-reads hit L2), so a full launch adds only the larger grid (8 B per extra frequency).
 # Valid only for the kernel source it was measured on (sha256 prefix of fpw_tile.cu + fpw_internal.cuh).
-TILE_TRAFFIC = {"source_sha256_16": "d18ef659d00a17c4", "bytes": 142.59e6, "nfreq": 20_000}
+TILE_TRAFFIC = {"source_sha256_16": "2d3f2bef95926030", "bytes": 143.19e6, "nfreq": 20_000}
 
 
 # ---------------------------------------------------------------- workload generation (spawned workers)
@@ -548,7 +548,8 @@ def run_configs(args):
         kms, n = ctx.kernel_time()
         ctx.set_timing(False)
         ev = float(w.offsets[-1]) * w.nfreq
-        return ev / (e0.elapsed_time(e1) / reps / 1e3), ev / (kms / max(n, 1) / 1e3), e0.elapsed_time(e1) / reps
+        kern = ev / (kms / n / 1e3) if n > 0 and kms > 0 else None
+        return ev / (e0.elapsed_time(e1) / reps / 1e3), kern, e0.elapsed_time(e1) / reps
 
     cases = [("single_plain", L.make("single_plain"), 10), ("single_ztf", L.make("single_ztf"), 20),
              ("ragged_10k", L.make("ragged_10k"), 20), ("precision", L.make("precision", range(20)), 20)]
@@ -558,7 +559,7 @@ def run_configs(args):
         call_rate, kern_rate, ms = timed(w, M, w.k, G.fpw_params_default())
         line = {"config": name, "curves": w.ncurves, "nobs": int(w.offsets[-1]), "nfreq": w.nfreq, "M": M,
                 "evals": float(w.offsets[-1]) * w.nfreq, "ms_per_call": ms, "evals_per_s_call": call_rate,
-                "evals_per_s_tile_kernel": kern_rate, "roofline_frac": kern_rate / peak}
+                "evals_per_s_tile_kernel": kern_rate, "roofline_frac": (kern_rate / peak) if kern_rate else None}
         if w.evals() <= 2e10:
             pr, _, _ = timed(w, M, w.k, G.fpw_params_default(phase_mode=G.FPW_PHASE_FP64), reps=1)
             line["plain_fp64_evals_per_s"] = pr

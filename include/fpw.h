@@ -139,7 +139,7 @@ FPW_API int fpw_periodogram_batch(const int64_t* offsets, int64_t ncurves, const
  *   S_out:        optional device float64[ncurves * nfreq] dense periodograms (NULL: not written)
  *   topk_idx/topk_S may be NULL when k == 0.
  * With params->phase_mode == FPW_PHASE_FP64 the plain binary64 form runs:
- * one launch per curve, binary64 phases and sums. */
+ * one launch per curve, binary64 phases and sums (M <= 100, else FPW_ENOTSUP). */
 FPW_API int fpw_periodogram_batch_ex(fpw_ctx* ctx, void* stream, const fpw_params* params, const int64_t* offsets,
                              const int64_t* offsets_host, int64_t ncurves, const double* t, const double* x,
                              const double* sigma, const double* freqs, int64_t nfreq, int M, int k,

@@ -545,6 +545,7 @@ int run_tile_path(fpw_ctx* ctx, const BatchCall& b) {
 
 // The binary64 plain form: per curve one periodogram launch (and one top-k launch).
 int run_plain_path(fpw_ctx* ctx, const BatchCall& b) {
+  if (plain_smem_bytes(b.M) > (size_t)ctx->smem_optin) return FPW_ENOTSUP;  // binary64 bins of one block
   unsigned* words = static_cast<unsigned*>(ctx->words.p);
   FPW_CK(cudaMemsetAsync(words, 0, 2 * sizeof(unsigned), b.stream));
   // validate frequencies (and observations) once for the status word
@@ -934,6 +935,7 @@ int fpw_periodogram_ex(fpw_ctx* ctx, void* stream, const fpw_params* params, con
   if (nfreq == 0) return FPW_OK;
   if (p.phase_mode == FPW_PHASE_FP64) {
     // single curve: the plain kernel reads the curve directly
+    if (plain_smem_bytes(M) > (size_t)ctx->smem_optin) return FPW_ENOTSUP;
     unsigned* words = static_cast<unsigned*>(ctx->words.p);
     FPW_CK(cudaMemsetAsync(words, 0, 2 * sizeof(unsigned), st));
     FPW_CK(ensure(ctx->curve_bad, 16));
