@@ -79,6 +79,11 @@ class Workload:
         a, b = int(self.offsets[c]), int(self.offsets[c + 1])
         return self.t[a:b], self.x[a:b], self.sigma[a:b]
 
+    def subset(self, cs) -> "Workload":
+        """The curves at positions ``cs`` of this workload (same grid, M and k)."""
+        curves = [(*self.curve(int(c)), self.periods[int(c)], self.kinds[int(c)]) for c in cs]
+        return _assemble(self.name, [int(self.curve_ids[int(c)]) for c in cs], curves, self.freqs, self.M, self.k)
+
 
 SPECS = {
     "single_plain": dict(wid=1, ncurves=1, M=10, k=5, f=(0.01, 50.0, 10_000)),

@@ -61,9 +61,16 @@ def test_single_observation_curves_and_k_beyond_peaks(ctx):
     S_or, o_idx, o_S = oracle.fpw_batch(w.offsets, w.t, w.x, w.sigma, w.freqs, 8, k=34)
     for c in range(w.ncurves):
         t, x, s = w.curve(c)
-        np.testing.assert_allclose(Sd[c], S_or[c], rtol=1e-5)
+        # two observations in one bin leave a binary64 rounding residue (~1e-32) of the mean-subtracted
+        # flux where FP32 gives 0: the absolute floor of the other parity tests covers it
+        assert_S_close(Sd[c], S_or[c], s_bound(x, s), what=f"curve {c} (n={t.size})")
         check_topk(idx[c], Sk[c], o_idx[c], o_S[c], o_dense=S_or[c], abs_tol=1e-7 * s_bound(x, s))
-        assert np.sum(idx[c] >= 0) == np.sum(o_idx[c][:30] >= 0)  # missing peaks reported as -1
+        valid = idx[c] >= 0
+        nv = int(valid.sum())
+        assert nv < 30 and valid[:nv].all()  # fewer peaks than k on 40 frequencies: the rest trail as -1
+        if t.size == 1:  # one observation: S is identically 0; the flat periodogram's one peak is its left end
+            assert np.all(S_or[c] == 0.0) and np.all(Sd[c] == 0.0)
+            assert nv == 1 and idx[c][0] == 0 and Sk[c][0] == 0.0
 
 
 def test_plain_form_rejects_bins_beyond_shared_memory(ctx):

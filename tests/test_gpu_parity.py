@@ -257,29 +257,3 @@ def test_plain_fp64_batch_form(ctx):
     for ci in range(w.ncurves):
         np.testing.assert_array_equal(idx[ci], o_idx[ci])
         np.testing.assert_array_equal(Sk[ci], o_S[ci].astype(np.float32))
-
-
-# ------------------------------------------------------------------ full-size workloads, sampled outputs
-def test_ragged_10k_full_size_sampled(ctx):
-    w = L.make("ragged_10k")
-    idx, Sk, _, st = run_batch(ctx, w)
-    assert st == 0
-    sample = np.random.default_rng(3).choice(w.ncurves, 12, replace=False)
-    sub = L.make("ragged_10k", sample)
-    _, o_idx, o_S = oracle.fpw_batch(sub.offsets, sub.t, sub.x, sub.sigma, sub.freqs, sub.M, dense=False, k=9)
-    for j, ci in enumerate(sample):
-        t, x, s = sub.curve(j)
-        check_topk(idx[ci], Sk[ci], o_idx[j], o_S[j], abs_tol=1e-7 * s_bound(x, s), what=f"ragged_10k curve {ci}")
-
-
-def test_sweep_batch_full_size_sampled(ctx):
-    """One 10^4-curve batch of the 10^5-curve sweep, as the benchmark launches it."""
-    w = L.make("sweep_100k", range(10_000))
-    idx, Sk, _, st = run_batch(ctx, w)
-    assert st == 0
-    sample = np.random.default_rng(4).choice(w.ncurves, 8, replace=False)
-    sub = L.make("sweep_100k", sample)
-    _, o_idx, o_S = oracle.fpw_batch(sub.offsets, sub.t, sub.x, sub.sigma, sub.freqs, sub.M, dense=False, k=9)
-    for j, ci in enumerate(sample):
-        t, x, s = sub.curve(j)
-        check_topk(idx[ci], Sk[ci], o_idx[j], o_S[j], abs_tol=1e-7 * s_bound(x, s), what=f"sweep curve {ci}")

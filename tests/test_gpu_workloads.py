@@ -1,0 +1,110 @@
+"""Every workload at its full size, launched as the benchmark launches it, against
+the oracle on sampled curves.
+
+Per workload: the whole batch runs once with the default parameters and top-k;
+for stratified sample curves the oracle computes the dense periodogram over the
+full grid, which checks the top-k of the full launch (tie-aware) and the dense S
+of a launch over the sample (away from bin edges); the bins of the sample's
+observations at the grid's highest frequencies (largest t f) are compared one
+by one. With FPW_WORKLOAD_REPORT set to a path, one JSON line per workload is
+appended there: pairs compared, bin mismatches (and how many lie farther than
+1e-9 cycles from an edge), S relative error, exact top-k agreement and the
+oracle's own evaluation rate on the host cores."""
+from __future__ import annotations
+
+import json
+import os
+import time
+
+import numpy as np
+import pytest
+
+import lightcurves as L
+import oracle
+from gpu_util import assert_S_close, check_topk, run_batch, s_bound, to_dev
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+NWIN = 2048  # frequencies per bin comparison (the top of the grid)
+SAMPLE = 4   # curves per workload
+
+WORKLOADS = [
+    ("single_plain", lambda: L.make("single_plain")),
+    ("single_ztf", lambda: L.make("single_ztf")),
+    ("ragged_10k", lambda: L.make("ragged_10k")),
+    ("precision", lambda: L.make("precision")),
+    ("sweep_100k M=10", lambda: L.make("sweep_100k", range(10_000), M=10)),
+    ("sweep_100k M=20", lambda: L.make("sweep_100k", range(10_000), M=20)),
+    ("sweep_100k M=50", lambda: L.make("sweep_100k", range(10_000), M=50)),
+]
+
+
+@pytest.fixture(scope="module")
+def G():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2502_00243_gb300 as G_
+    return G_
+
+
+def stratified(offsets, count):
+    n = offsets[1:] - offsets[:-1]
+    order = np.argsort(n, kind="stable")
+    pick = np.linspace(0, len(order) - 1, min(count, len(order))).round().astype(int)
+    return np.unique(order[pick])
+
+
+@pytest.mark.parametrize("name,make", WORKLOADS, ids=[w[0] for w in WORKLOADS])
+def test_workload_full_size_sampled(G, name, make):
+    w = make()
+    M, k = w.M, w.k
+    ctx = G.Context(0)
+    idx, Sk, _, st = run_batch(ctx, w)  # the full batch, as the benchmark launches it
+    assert st == 0
+    pick = stratified(w.offsets, SAMPLE)
+    sub = w.subset(pick)
+    _, _, Sd, st = run_batch(ctx, sub, dense=True)
+    assert st == 0
+    cores = os.cpu_count() or 1
+    rep = dict(workload=name, curves=int(w.ncurves), nobs=int(w.offsets[-1]), nfreq=int(w.nfreq), M=M, k=k,
+               sample_curves=[int(c) for c in pick], pairs=0, bin_mismatch=0, mismatch_beyond_1e9=0,
+               topk_exact=0, topk_curves=0, oracle_evals=0.0, oracle_seconds=0.0, cores=cores)
+    errs = []
+    fr_top = w.freqs[-NWIN:]
+    for j, c in enumerate(pick):
+        t, x, s = sub.curve(j)
+        t0 = time.perf_counter()
+        S_or = oracle.fpw_parallel(t, x, s, w.freqs, M, nthreads=cores)
+        rep["oracle_seconds"] += time.perf_counter() - t0
+        rep["oracle_evals"] += float(t.size) * w.nfreq
+        near = oracle.min_edge_parallel(t, w.freqs, M, nthreads=cores) <= 1e-9 if t.size else np.zeros(w.nfreq, bool)
+        bound = s_bound(x, s)
+        assert_S_close(Sd[j], S_or, bound, mask=~near, what=f"{name} curve {c}")
+        ok = ~near & (np.abs(S_or) > 1e-6 * bound)
+        if ok.any():
+            errs.append(np.abs(Sd[j][ok] - S_or[ok]) / np.abs(S_or[ok]))
+        o_idx, o_S = oracle.topk(S_or, k + 4)
+        check_topk(idx[c], Sk[c], o_idx, o_S, abs_tol=1e-7 * bound, o_dense=S_or, what=f"{name} curve {c} peaks")
+        rep["topk_curves"] += 1
+        rep["topk_exact"] += int(np.array_equal(idx[c], o_idx[:k]))
+        if t.size:
+            tt, ff = torch.from_numpy(t).cuda(), torch.from_numpy(fr_top).cuda()
+            out = torch.empty(fr_top.size * t.size, dtype=torch.int32, device="cuda")
+            G.fpw_debug_bins(ctx, None, None, tt, ff, M, out)
+            gb = out.cpu().numpy().reshape(fr_top.size, t.size)
+            ob, e = oracle.bins(t, fr_top, M)
+            mm = gb != ob
+            rep["pairs"] += int(mm.size)
+            rep["bin_mismatch"] += int(mm.sum())
+            rep["mismatch_beyond_1e9"] += int((mm & (e > 1e-9)).sum())
+    assert rep["mismatch_beyond_1e9"] == 0
+    e = np.concatenate(errs) if errs else np.zeros(1)
+    rep.update(S_rel_err_max=float(e.max()), S_rel_err_median=float(np.median(e)),
+               bin_mismatch_rate=rep["bin_mismatch"] / max(rep["pairs"], 1),
+               oracle_evals_per_s=rep["oracle_evals"] / max(rep["oracle_seconds"], 1e-9))
+    path = os.environ.get("FPW_WORKLOAD_REPORT")
+    if path:
+        with open(path, "a") as fh:
+            fh.write(json.dumps(rep) + "\n")
+    ctx.close()
