@@ -79,6 +79,8 @@ def _load():
             lib.oracle_bins.restype = c_int
             lib.oracle_fpw_multi.argtypes = [vp, vp, vp, i64, vp, i64, c_int, c_int, d, vp]
             lib.oracle_fpw_multi.restype = c_int
+            lib.oracle_fpw_shared.argtypes = [vp, i64, i64, vp, vp, vp, i64, c_int, d, vp]
+            lib.oracle_fpw_shared.restype = c_int
             lib.oracle_phase_entropy.argtypes = [vp, i64, vp, i64, c_int, vp]
             lib.oracle_phase_entropy.restype = c_int
             lib.oracle_min_edge.argtypes = [vp, i64, vp, i64, c_int, vp]
@@ -122,6 +124,20 @@ def fpw_multi(t, x, sigma, freqs, M_max: int, g: int, inv_alpha2: float = 0.0) -
     S = np.empty((int(g), freqs.shape[0]), dtype=np.float64)
     _check(lib.oracle_fpw_multi(_ptr(t), _ptr(x), _ptr(sigma), t.shape[0], _ptr(freqs), freqs.shape[0], int(M_max),
                                 int(g), float(inv_alpha2), _ptr(S)))
+    return S
+
+
+def fpw_shared(t, x, sigma, freqs, M: int, inv_alpha2: float = 0.0) -> np.ndarray:
+    """Section 4 / Appendix D batch routine: curves sharing the times ``t``
+    (``x`` and ``sigma`` of shape ``[C, n]``), bins computed once per
+    frequency: array ``[C, F]``; NaN rows for curves with invalid data."""
+    lib = _load()
+    t, freqs = _f64(t), _f64(freqs)
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.float64).reshape(-1, t.shape[0]))
+    sigma = np.ascontiguousarray(np.asarray(sigma, dtype=np.float64).reshape(x.shape))
+    S = np.empty((x.shape[0], freqs.shape[0]), dtype=np.float64)
+    _check(lib.oracle_fpw_shared(_ptr(t), t.shape[0], x.shape[0], _ptr(x), _ptr(sigma), _ptr(freqs), freqs.shape[0],
+                                 int(M), float(inv_alpha2), _ptr(S)))
     return S
 
 

@@ -115,6 +115,66 @@ int oracle_fpw(const double* t, const double* x, const double* sigma, int64_t n,
   return ORACLE_OK;
 }
 
+/* Section 4 and Appendix D (the batch routine): several light curves observed
+ * at the same times t. For each trial frequency the bin of every observation
+ * is computed once, then each curve's Eq. 1 statistic is formed from those
+ * bins: S_out[c * nfreq + k] for curve c, whose fluxes and uncertainties are
+ * x[c * n + i] and sigma[c * n + i]. A curve with a non-finite value or a
+ * sigma <= 0 gets NaN at every frequency; non-finite t or f is an error. */
+int oracle_fpw_shared(const double* t, int64_t n, int64_t ncurves, const double* x, const double* sigma,
+                      const double* freqs, int64_t nfreq, int M, double inv_alpha2, double* S_out) {
+  if (n < 0 || ncurves < 0 || nfreq < 0 || M < 1 || !(inv_alpha2 >= 0.0)) return ORACLE_EINVAL;
+  if (nfreq > 0 && ncurves > 0 && (!freqs || !S_out)) return ORACLE_EINVAL;
+  if (n > 0 && (!t || (ncurves > 0 && (!x || !sigma)))) return ORACLE_EINVAL;
+  for (int64_t k = 0; k < nfreq; ++k)
+    if (!isfinite(freqs[k])) return ORACLE_EDATA;
+  for (int64_t i = 0; i < n; ++i)
+    if (!isfinite(t[i])) return ORACLE_EDATA;
+  int* bin = (int*)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+  char* bad = (char*)malloc((size_t)(ncurves > 0 ? ncurves : 1));
+  double* A = (double*)malloc(sizeof(double) * (size_t)M);
+  double* B = (double*)malloc(sizeof(double) * (size_t)M);
+  if (!bin || !bad || !A || !B) {
+    free(bin);
+    free(bad);
+    free(A);
+    free(B);
+    return ORACLE_ENOMEM;
+  }
+  for (int64_t c = 0; c < ncurves; ++c) bad[c] = check_curve(t, x + c * n, sigma + c * n, n) != ORACLE_OK;
+  for (int64_t k = 0; k < nfreq; ++k) {
+    for (int64_t i = 0; i < n; ++i) bin[i] = oracle_bin(t[i], freqs[k], M);
+    for (int64_t c = 0; c < ncurves; ++c) {
+      if (bad[c]) {
+        S_out[c * nfreq + k] = NAN;
+        continue;
+      }
+      const double* xc = x + c * n;
+      const double* sc = sigma + c * n;
+      for (int m = 0; m < M; ++m) {
+        A[m] = 0.0;
+        B[m] = 0.0;
+      }
+      for (int64_t i = 0; i < n; ++i) {
+        double w = 1.0 / (sc[i] * sc[i]);
+        A[bin[i]] += xc[i] * w;
+        B[bin[i]] += w;
+      }
+      double S = 0.0;
+      for (int m = 0; m < M; ++m) {
+        double den = B[m] + inv_alpha2;
+        if (den > 0.0) S += (A[m] * A[m]) / den;
+      }
+      S_out[c * nfreq + k] = S;
+    }
+  }
+  free(bin);
+  free(bad);
+  free(A);
+  free(B);
+  return ORACLE_OK;
+}
+
 /* Section 3.4, S_FPW for several numbers of bins from one pass: the bin sums
  * at M_max bins are combined into M = M_max / g bins, for each of the g bin
  * offsets o: combined bin j of offset o holds the M_max-bins

@@ -37,6 +37,11 @@ MUTATIONS = {
     "ends_never_peaks": ("if (k == 0) return S[0] >= S[1];", "if (k == 0) return 0;"),
     "multi_ignores_offset": ("int m = (j * g + o + u) % M_max;", "int m = (j * g + u) % M_max;"),
     "multi_offset_backwards": ("int m = (j * g + o + u) % M_max;", "int m = (j * g - o + u + M_max) % M_max;"),
+    "shared_flux_of_first_curve": ("const double* xc = x + c * n;", "const double* xc = x;"),
+    "shared_sigma_of_first_curve": ("const double* sc = sigma + c * n;", "const double* sc = sigma;"),
+    "shared_bins_not_recomputed": ("    for (int64_t i = 0; i < n; ++i) bin[i] = oracle_bin(t[i], freqs[k], M);",
+                                   "    if (k == 0)\n      for (int64_t i = 0; i < n; ++i) bin[i] = oracle_bin(t[i], freqs[k], M);"),
+    "shared_unweighted_numerator": ("A[bin[i]] += xc[i] * w;", "A[bin[i]] += xc[i];"),
     "edge_distance_drops_product_error": ("return fabs(r + (ue + (double)M * e)) / (double)M;",
                                           "return fabs(r + ue) / (double)M;"),
 }
@@ -50,7 +55,16 @@ class Api:
         lib.oracle_topk.argtypes = [vp, i64, ci, ci, vp, vp]
         lib.oracle_bins.argtypes = [vp, i64, vp, i64, ci, vp, vp]
         lib.oracle_fpw_multi.argtypes = [vp, vp, vp, i64, vp, i64, ci, ci, d, vp]
+        lib.oracle_fpw_shared.argtypes = [vp, i64, i64, vp, vp, vp, i64, ci, d, vp]
         self.lib = lib
+
+    def fpw_shared(self, t, x, sigma, freqs, M, c=0.0):
+        t, x, sigma, freqs = (np.ascontiguousarray(a, dtype=np.float64) for a in (t, x, sigma, freqs))
+        S = np.empty((x.shape[0], freqs.shape[0]))
+        rc = self.lib.oracle_fpw_shared(t.ctypes.data, t.shape[0], x.shape[0], x.ctypes.data, sigma.ctypes.data,
+                                        freqs.ctypes.data, freqs.shape[0], M, c, S.ctypes.data)
+        assert rc == 0
+        return S
 
     def fpw_multi(self, t, x, sigma, freqs, M_max, g, c=0.0):
         t, x, sigma, freqs = (np.ascontiguousarray(a, dtype=np.float64) for a in (t, x, sigma, freqs))
@@ -145,6 +159,18 @@ def battery(api: Api) -> list[str]:
             bins.append(int(math.floor(ph * 4)))
         if not np.isclose(S[o, 0], least_squares_reduction(x, sigma, np.array(bins), 4), rtol=1e-9, atol=1e-10):
             failed.append("multi_m")
+            break
+    # curves sharing their times: each row is the dense form with the shared exact bins
+    rng = np.random.default_rng(21)
+    t = rng.uniform(0, 30, 9)
+    x = rng.normal(0, 1, (3, 9))
+    sigma = rng.uniform(0.3, 2.0, (3, 9))
+    fs = np.array([0.7, 1.9])
+    S = api.fpw_shared(t, x, sigma, fs, 3, 1.0)
+    for q, f in enumerate(fs):
+        b, _ = exact_bins(t, f, 3)
+        if not all(np.isclose(S[c, q], dense_chi2_difference(x[c], sigma[c], b, 3, 1.0), rtol=1e-9) for c in range(3)):
+            failed.append("shared")
             break
     # top-k golden cases
     idx, _ = api.topk(np.array([1.0, 3.0, 2.0, 5.0, 5.0, 4.0, 6.0]), 3)

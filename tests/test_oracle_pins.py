@@ -430,3 +430,43 @@ def test_phase_entropy_ignores_order_and_fluxes():
     H = oracle.phase_entropy(t, f, 20)
     np.testing.assert_allclose(oracle.phase_entropy(t[::-1].copy(), f, 20), H, rtol=1e-13)
     assert np.all(H >= 0) and np.all(H <= math.log(20) + 1e-12)
+
+
+# ---------------------------------------------------------------- shared-timestamp batch (Section 4, Appendix D)
+@pytest.mark.parametrize("seed", range(6))
+def test_shared_batch_dense_form_with_one_bin_matrix(seed):
+    """All curves use one exact bin matrix per frequency: the dense Appendix A.3
+    form per curve with that shared matrix."""
+    rng = np.random.default_rng([31, seed])
+    n, C, M, alpha = int(rng.integers(1, 11)), 3, int(rng.choice([2, 3, 4])), 1.5
+    t = rng.uniform(-20.0 if seed % 2 else 0.0, 20.0, n)
+    x = rng.normal(0, 1, (C, n))
+    sigma = rng.uniform(0.3, 2.0, (C, n))
+    freqs = rng.uniform(0.05, 3.0, 3)
+    S = oracle.fpw_shared(t, x, sigma, freqs, M, 1.0 / alpha ** 2)
+    for q, f in enumerate(freqs):
+        b, _ = exact_bins(t, f, M)
+        for c in range(C):
+            assert S[c, q] == pytest.approx(dense_chi2_difference(x[c], sigma[c], b, M, alpha), rel=1e-9, abs=1e-12)
+
+
+def test_shared_batch_equals_single_curve_oracle_and_permutes_rows():
+    w = L.make("single_ztf", nfreq=3000)
+    t = w.t
+    rng = np.random.default_rng(5)
+    C = 5
+    x = np.stack([w.x] + [rng.normal(0, 0.1, t.size) for _ in range(C - 1)])
+    sigma = np.stack([w.sigma] + [rng.uniform(0.02, 0.2, t.size) for _ in range(C - 1)])
+    S = oracle.fpw_shared(t, x, sigma, w.freqs, 20)
+    for c in range(C):  # same arithmetic in the same order per curve: bitwise equal
+        np.testing.assert_array_equal(S[c], oracle.fpw(t, x[c], sigma[c], w.freqs, 20))
+    perm = rng.permutation(C)
+    np.testing.assert_array_equal(oracle.fpw_shared(t, x[perm], sigma[perm], w.freqs, 20), S[perm])
+    # a curve with invalid data gives a NaN row and leaves the others unchanged
+    sigma_bad = sigma.copy()
+    sigma_bad[2, 7] = 0.0
+    S_bad = oracle.fpw_shared(t, x, sigma_bad, w.freqs, 20)
+    assert np.isnan(S_bad[2]).all()
+    np.testing.assert_array_equal(S_bad[[0, 1, 3, 4]], S[[0, 1, 3, 4]])
+    with pytest.raises(oracle.OracleError):
+        oracle.fpw_shared(np.array([0.0, np.inf]), np.zeros((1, 2)), np.ones((1, 2)), w.freqs[:3], 4)
