@@ -46,7 +46,7 @@ KERNELS_PER_STEP = 5  # prep, tile_dev, tile, merge, latch
 # reads each curve from DRAM once per launch (t and the staged weights, about 16.7 B per observation;
 # per-tile re-reads hit L2), so a full launch adds only the larger grid (8 B per extra frequency).
 # Valid only for the kernel source it was measured on (sha256 prefix of fpw_tile.cu + fpw_internal.cuh).
-TILE_TRAFFIC = {"source_sha256_16": "2d3f2bef95926030", "bytes": 143.19e6, "nfreq": 20_000}
+TILE_TRAFFIC = {"source_sha256_16": "22ded89c0d53e517", "bytes": 143.55e6, "nfreq": 20_000}
 
 
 # ---------------------------------------------------------------- workload generation (spawned workers)
@@ -186,6 +186,15 @@ class ClockSampler:
 def env_rank():
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
             int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def peak_bf16_tflops():
+    """Measured dense bf16 burst peak (fp16 runs at the same nominal rate)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["bf16_tflops"])
+    except (OSError, KeyError, ValueError):
+        return 1900.0  # earlier GB300 measurement
 
 
 def sm_max_mhz():
@@ -538,6 +547,44 @@ def run_configs(args):
             line["graph_ms_per_call"] = gms
             line["graph_evals_per_s_call"] = gr
         print(json.dumps(line), flush=True)
+
+    # curves sharing their times: the tensor-core path against the batched path on the same curves
+    w = L.make("shared_4096")
+    C, n = w.ncurves, L.SHARED_N
+    d = [torch.from_numpy(np.ascontiguousarray(a)).cuda()
+         for a in (w.t[:n], w.x.reshape(C, n), w.sigma.reshape(C, n), w.freqs)]
+    idx = torch.empty(C * w.k, dtype=torch.int32, device="cuda")
+    Sk = torch.empty(C * w.k, dtype=torch.float32, device="cuda")
+    call = lambda: G.fpw_periodogram_shared(ctx, None, None, d[0], d[1], d[2], d[3], w.M, w.k, idx, Sk)
+    call()
+    torch.cuda.synchronize()
+    ctx.set_timing(True)
+    ctx.kernel_time()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 3
+    e0.record()
+    for _ in range(reps):
+        call()
+    e1.record()
+    torch.cuda.synchronize()
+    kms, nl = ctx.kernel_time()
+    ctx.set_timing(False)
+    ev = float(C) * n * w.nfreq
+    fpm = 256 // w.M
+    n_mma = -(-fpm * w.M // 16) * 16
+    npass = -(-w.nfreq // (2 * fpm))
+    flops = 2.0 * 128 * 2 * n_mma * (-(-n // 32) * 64) * npass * (-(-C // 64))  # issued MMA flops per call
+    kern_s = kms / nl / 1e3
+    tile_rate, tile_kern, _ = timed(w, w.M, w.k, G.fpw_params_default())
+    line = {"config": "shared_4096 (4096 curves sharing N=1000 times, M=20, 5e5 freqs, top-5)", "curves": C,
+            "nobs_shared": n, "nfreq": w.nfreq, "M": w.M, "evals": ev,
+            "ms_per_call": e0.elapsed_time(e1) / reps, "evals_per_s_call": ev / (e0.elapsed_time(e1) / reps / 1e3),
+            "evals_per_s_mma_kernel": ev / kern_s,
+            "mma_tflops_issued": flops / kern_s / 1e12,
+            "tensor_frac_of_measured_bf16_peak": flops / kern_s / 1e12 / peak_bf16_tflops(),
+            "batched_path_same_curves_evals_per_s_call": tile_rate,
+            "batched_path_same_curves_evals_per_s_tile_kernel": tile_kern}
+    print(json.dumps(line), flush=True)
     ctx.close()
     return 0
 

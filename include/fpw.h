@@ -165,6 +165,28 @@ FPW_API int fpw_periodogram_batch_multi(fpw_ctx* ctx, void* stream, const fpw_pa
                                         int M_max, const int* groups, int ngroups, int k, int32_t* topk_idx,
                                         int32_t* topk_offset, float* topk_S, double* S_out);
 
+/* Curves that share one set of observation times (Section 4 and the batch
+ * routine of Appendix D: many light curves of one field observed in the same
+ * exposures). Eq. 1 per curve with the bins computed once per (observation,
+ * frequency); on GB300 the bin sums of 64 curves at a time are one tensor-core
+ * product of the fp16 hi/lo split of (x w, w) with the one-hot bin matrix
+ * (FP32 accumulation), so the result matches FP32 bin sums of the batched call.
+ *   t:        device float64[n], the shared times (finite)
+ *   x, sigma: device float64[ncurves * n], curve c's values at [c * n + i]
+ *   freqs:    device float64[nfreq] (any grid; phases are exact per frequency)
+ *   M:        1 <= M <= 256
+ *   k, topk_idx, topk_S, S_out: as fpw_periodogram_batch_ex (S_out optional,
+ *             float64[ncurves * nfreq], the FP32 statistic widened)
+ * params: FPW_PHASE_FIXED64 and FPW_ACCUM_FP32 only (FPW_ENOTSUP otherwise);
+ * inv_alpha2 and peak_mode apply. A curve with sigma <= 0 or a non-finite value
+ * gets S = NaN and no peaks (status FPW_EDATA). Scratch held by the context:
+ * 8 n bytes per curve (rounded up to 64 curves x 32 observations) and, when
+ * k > 0, a dense FP32 periodogram of 4 ncurves nfreq bytes.
+ * Stream-ordered. Errors: FPW_EINVAL, FPW_ENOTSUP, FPW_ENOMEM, FPW_ECUDA. */
+FPW_API int fpw_periodogram_shared(fpw_ctx* ctx, void* stream, const fpw_params* params, const double* t, int64_t n,
+                                   int64_t ncurves, const double* x, const double* sigma, const double* freqs,
+                                   int64_t nfreq, int M, int k, int32_t* topk_idx, float* topk_S, double* S_out);
+
 /* Phase entropy (Appendix C) of one set of observation times at every trial
  * frequency: H(f) = -sum_m (N_m/N) log(N_m/N), N_m the observations in phase bin
  * m (bins as the periodogram kernels assign them), natural logarithm, FP32.

@@ -22,6 +22,10 @@ curves with ZTF-like cadence and noise stand in for them):
   500 1/d (t*f up to 1e6 cycles), M = 20.
 * ``sweep_100k``    -- 1e5 curves, N log-uniform 100-3000, mixed waveforms as
   ``ragged_10k``, M in {10, 20, 50}, 5e5 frequencies 0.01-50 1/d, top-5.
+* ``shared_4096``   -- 4096 curves of one field observed in the same exposures:
+  one ZTF-like cadence of N = 1000 times shared by all, per-curve waveforms,
+  amplitudes and sigma as ``ragged_10k``, M = 20, 5e5 frequencies 0.01-50 1/d,
+  top-5 (the shared-timestamp batch).
 
 Cadence model: seasons of 240 days starting every 365 days; nights about 3 days
 apart (3 +- 0.5 d); each night holds visit pairs 30 min apart starting
@@ -91,7 +95,15 @@ SPECS = {
     "ragged_10k": dict(wid=3, ncurves=10_000, M=20, k=5, f=(0.02, 50.0, 200_000)),
     "precision": dict(wid=4, ncurves=100, M=20, k=5, f=(0.01, 500.0, 2_000_000)),
     "sweep_100k": dict(wid=5, ncurves=100_000, M=20, k=5, f=(0.01, 50.0, 500_000)),
+    "shared_4096": dict(wid=6, ncurves=4096, M=20, k=5, f=(0.01, 50.0, 500_000)),
 }
+
+SHARED_N = 1000
+
+
+def shared_times() -> np.ndarray:
+    """The observation times every ``shared_4096`` curve shares."""
+    return ztf_cadence(np.random.default_rng([SPECS["shared_4096"]["wid"]]), SHARED_N)
 
 
 def freq_grid(name: str) -> np.ndarray:
@@ -170,6 +182,14 @@ def _curve(name: str, c: int):
             n = int(round(float(_loguniform(rng, 100.0, 3000.0))))
         t = ztf_cadence(rng, n)
         sigma = _loguniform(rng, 0.01, 0.3, n)
+        kind = WAVEFORMS[int(rng.integers(0, 4))]
+        period = float(_loguniform(rng, 0.05, 50.0))
+        amp = float(_loguniform(rng, 0.2, 5.0)) * float(np.median(sigma))
+        x = _finish(rng, t, waveform(kind, t, period, rng.uniform(0.0, 1.0), amp), sigma)
+        return t, x, sigma, (period if kind != "noise" else float("nan")), kind
+    if name == "shared_4096":
+        t = shared_times()
+        sigma = _loguniform(rng, 0.01, 0.3, t.shape[0])
         kind = WAVEFORMS[int(rng.integers(0, 4))]
         period = float(_loguniform(rng, 0.05, 50.0))
         amp = float(_loguniform(rng, 0.2, 5.0)) * float(np.median(sigma))

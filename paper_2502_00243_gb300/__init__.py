@@ -30,7 +30,7 @@ EXPORTED = ("fpw_params_default", "fpw_ctx_create", "fpw_ctx_destroy", "fpw_ctx_
             "fpw_periodogram_ex", "fpw_periodogram_batch", "fpw_periodogram_batch_ex", "fpw_periodogram_batch_host",
             "fpw_debug_bins", "fpw_strerror", "fpw_version", "fpw_last_cuda_error", "fpw_ctx_set_timing",
             "fpw_ctx_kernel_time", "fpw_periodogram_batch_noalloc", "fpw_ctx_set_shape", "fpw_ctx_clear_shapes",
-            "fpw_periodogram_batch_multi", "fpw_phase_entropy", "fpw_phase_entropy_peaks")
+            "fpw_periodogram_batch_multi", "fpw_phase_entropy", "fpw_phase_entropy_peaks", "fpw_periodogram_shared")
 
 
 class FPWError(RuntimeError):
@@ -88,6 +88,7 @@ def lib():
                 "fpw_ctx_set_shape": (ci, [vp, ci, ci, i64, i64, ci, ci, ci]),
                 "fpw_ctx_clear_shapes": (ci, [vp]),
                 "fpw_phase_entropy": (ci, [vp, vp, vp, i64, vp, i64, ci, vp]),
+                "fpw_periodogram_shared": (ci, [vp, vp, P, vp, i64, i64, vp, vp, vp, i64, ci, ci, vp, vp, vp]),
                 "fpw_phase_entropy_peaks": (ci, [vp, vp, vp, i64, vp, vp, i64, ci, ci, vp, vp, vp]),
                 "fpw_periodogram_batch_multi": (ci, [vp, vp, P, vp, vp, i64, vp, vp, vp, vp, i64, ci, vp, ci, ci, vp, vp,
                                                      vp, vp]),
@@ -284,6 +285,24 @@ def fpw_periodogram_batch_multi(ctx: Context, stream, params, offsets, offsets_h
         _dev(S_out, torch.float64, "S_out") if S_out is not None else None)
     _check(rc, "fpw_periodogram_batch_multi")
     return topk_idx, topk_offset, topk_S, S_out
+
+
+def fpw_periodogram_shared(ctx: Context, stream, params, t, x, sigma, freqs, M: int, k: int, topk_idx=None,
+                           topk_S=None, S_out=None):
+    """Curves sharing the times ``t``: ``x`` and ``sigma`` are ``[C, n]`` CUDA
+    tensors (row per curve); top-k ``[C * k]`` and optional dense ``S_out``
+    ``[C * F]`` as for the batched call."""
+    import torch
+    if x.dim() != 2 or sigma.shape != x.shape or x.shape[1] != t.numel():
+        raise ValueError("x and sigma must be [ncurves, n] with n = t.numel()")
+    rc = lib().fpw_periodogram_shared(
+        ctx.handle, _stream(stream), _params(params), _dev(t, torch.float64, "t"), t.numel(), x.shape[0],
+        _dev(x, torch.float64, "x"), _dev(sigma, torch.float64, "sigma"), _dev(freqs, torch.float64, "freqs"),
+        freqs.numel(), int(M), int(k),
+        _dev(topk_idx, torch.int32, "topk_idx") if topk_idx is not None else None,
+        _dev(topk_S, torch.float32, "topk_S") if topk_S is not None else None,
+        _dev(S_out, torch.float64, "S_out") if S_out is not None else None)
+    _check(rc, "fpw_periodogram_shared")
 
 
 def fpw_phase_entropy(ctx: Context, stream, t, freqs, M: int, H_out):

@@ -14,7 +14,7 @@
 #include <new>
 #include <vector>
 
-#include "fpw_internal.cuh"
+#include "fpw_shared.cuh"
 
 using namespace fpw;
 
@@ -123,6 +123,7 @@ struct fpw_ctx {
   cudaStream_t last_stream = nullptr;
   cudaStream_t own_stream = nullptr;
   DevBuf aw, cand_S, cand_idx, curve_bad, words, dense, tile_dev;
+  DevBuf sh_image, sh_scale, sh_S32;  // shared-timestamp path scratch
   DevBuf h_off, h_t, h_x, h_sigma, h_freqs, h_idx, h_S;  // device copies for the host entry point
   std::vector<int64_t> off_host;                          // host copy of offsets (when not supplied)
   std::vector<Plan*> plans;
@@ -686,6 +687,7 @@ int fpw_ctx_create(fpw_ctx** out, int device) {
     e = tile_init_attributes(ctx->smem_optin);
   }
   if (e == cudaSuccess) e = plain_init_attributes(ctx->smem_optin);
+  if (e == cudaSuccess && (size_t)ctx->smem_optin >= shared_smem_bytes()) e = shared_init_attributes();
   if (e == cudaSuccess) e = ensure(ctx->words, 64);
   if (e == cudaSuccess) e = cudaMemset(ctx->words.p, 0, 64);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking);
@@ -713,7 +715,8 @@ int fpw_ctx_destroy(fpw_ctx* ctx) {
     }
     ctx->plans.clear();
     for (DevBuf* b : {&ctx->aw, &ctx->cand_S, &ctx->cand_idx, &ctx->curve_bad, &ctx->words, &ctx->dense, &ctx->tile_dev, &ctx->h_off,
-                      &ctx->h_t, &ctx->h_x, &ctx->h_sigma, &ctx->h_freqs, &ctx->h_idx, &ctx->h_S})
+                      &ctx->h_t, &ctx->h_x, &ctx->h_sigma, &ctx->h_freqs, &ctx->h_idx, &ctx->h_S, &ctx->sh_image,
+                      &ctx->sh_scale, &ctx->sh_S32})
       free_buf(*b);
     if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
     for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
@@ -1027,6 +1030,81 @@ int fpw_periodogram_batch_host(fpw_ctx* ctx, const fpw_params* params, const int
     FPW_CK(cudaMemcpyAsync(topk_S, ctx->h_S.p, sizeof(float) * (size_t)(ncurves * k), cudaMemcpyDeviceToHost, st));
   }
   return sync_status(ctx, st, FPW_OK);
+}
+
+int fpw_periodogram_shared(fpw_ctx* ctx, void* stream, const fpw_params* params, const double* t, int64_t n,
+                           int64_t ncurves, const double* x, const double* sigma, const double* freqs, int64_t nfreq,
+                           int M, int k, int32_t* topk_idx, float* topk_S, double* S_out) {
+  if (!ctx || n < 0 || ncurves < 0 || nfreq < 0 || M < 1 || k < 0 || k > FPW_MAX_TOPK) return FPW_EINVAL;
+  if (ncurves > 0 && nfreq > 0 && !freqs) return FPW_EINVAL;
+  if (ncurves > 0 && n > 0 && (!t || !x || !sigma)) return FPW_EINVAL;
+  if (ncurves > 0 && k > 0 && (!topk_idx || !topk_S)) return FPW_EINVAL;
+  if (nfreq > ((int64_t)1 << 31) - 1024 || ncurves > ((int64_t)1 << 31) - 1) return FPW_EINVAL;
+  fpw_params p;
+  fpw_params_default(&p);
+  if (params) p = *params;
+  if (!valid_params(p)) return FPW_EINVAL;
+  if (p.phase_mode != FPW_PHASE_FIXED64 || p.accum != FPW_ACCUM_FP32) return FPW_ENOTSUP;
+  int n_mma = 0;
+  const int fpm = shared_freqs_per_mma(M, &n_mma);
+  if (fpm == 0) return FPW_ENOTSUP;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return FPW_ECUDA;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  clear_stale_error();
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  ctx->last_stream = st;
+  if ((size_t)ctx->smem_optin < shared_smem_bytes()) return FPW_ENOTSUP;
+  if (ncurves == 0) return FPW_OK;
+  unsigned* words = static_cast<unsigned*>(ctx->words.p);
+  if (nfreq == 0) {
+    if (k > 0) FPW_CK(launch_fill_topk(topk_idx, topk_S, ncurves * k, st));
+    return FPW_OK;
+  }
+  const int64_t per = shared_curves_per_group();
+  SharedArgs a{};
+  a.t = t;
+  a.n = n;
+  a.ncurves = ncurves;
+  a.x = x;
+  a.sigma = sigma;
+  a.freqs = freqs;
+  a.nfreq = nfreq;
+  a.M = M;
+  a.fpm = fpm;
+  a.n_mma = n_mma;
+  a.npass = (nfreq + 2 * fpm - 1) / (2 * fpm);
+  a.ngroups = (ncurves + per - 1) / per;
+  a.nchunks = (n + 31) / 32;
+  a.inv_alpha2 = p.inv_alpha2;
+  a.k = k;
+  a.peak_raw = p.peak_mode == FPW_PEAK_RAW ? 1 : 0;
+  a.topk_idx = topk_idx;
+  a.topk_S = topk_S;
+  a.S_out = S_out;
+  FPW_CK(ensure(ctx->sh_image, std::max<size_t>(shared_image_bytes(ncurves, n), 256)));
+  FPW_CK(ensure(ctx->sh_scale, (size_t)(a.ngroups * per) * 2 * sizeof(float)));
+  FPW_CK(ensure(ctx->curve_bad, (size_t)(a.ngroups * per) + 16));
+  if (k > 0) FPW_CK(ensure(ctx->sh_S32, (size_t)ncurves * (size_t)nfreq * sizeof(float)));
+  a.image = static_cast<unsigned char*>(ctx->sh_image.p);
+  a.inv_scale = static_cast<float*>(ctx->sh_scale.p);
+  a.curve_bad = static_cast<uint8_t*>(ctx->curve_bad.p);
+  a.S32 = k > 0 ? static_cast<float*>(ctx->sh_S32.p) : nullptr;
+  a.status = words + 1;
+  if (ctx->timing) {
+    while (ctx->ev.size() < ctx->ev_used + 2) {
+      cudaEvent_t e;
+      FPW_CK(cudaEventCreate(&e));
+      ctx->ev.push_back(e);
+    }
+    a.timing_start = ctx->ev[ctx->ev_used];
+    a.timing_stop = ctx->ev[ctx->ev_used + 1];
+    ctx->ev_used += 2;
+  }
+  FPW_CK(cudaMemsetAsync(words, 0, 2 * sizeof(unsigned), st));
+  FPW_CK(launch_shared(a, ctx->nsm, st));
+  FPW_CK(launch_latch(words, st));
+  return FPW_OK;
 }
 
 int fpw_phase_entropy(fpw_ctx* ctx, void* stream, const double* t, int64_t n, const double* freqs, int64_t nfreq,

@@ -265,26 +265,65 @@ __device__ __forceinline__ void accumulate_tile(const TileArgs& args, const Bloc
       // The next observation's staged data is loaded before this one's bin
       // stores (the compiler cannot move it there itself: both are shared
       // memory), so the broadcast-load latency overlaps the bin updates.
-      ulonglong2 pd = sPD[0];
-      A2 aw = sAW[0];
-#pragma unroll 2
-      for (int i = 0; i < cnt; ++i) {
-        const int in = (i + 1 < cnt) ? i + 1 : i;
-        const ulonglong2 pdn = sPD[in];
-        const A2 awn = sAW[in];
-        // the R phases are independent multiply-adds (no serial chain of 64-bit adds)
-        const unsigned long long phi0 = pd.x + (unsigned long long)j0 * pd.y;
+      if (R == 2) {
+        // Software-pipelined (measured faster only at R = 2, where the phase ->
+        // bin -> offset chain is a larger share of each iteration): the bin
+        // offsets of observation i + 1 are computed while observation i's bin
+        // loads are in flight, from staged data loaded one iteration earlier.
+        // Same adds in the same order as the loop below.
         unsigned off[R];
+        {
+          const ulonglong2 p0 = sPD[0];
+          const unsigned long long f0 = p0.x + (unsigned long long)j0 * p0.y;
 #pragma unroll
-        for (int r = 0; r < R; ++r)
-          off[r] = bin_of_phase(phi0 + (unsigned long long)r * pd.y, M) * T8 + (unsigned)r * MT8;
-        A2 v[R];
+          for (int r = 0; r < R; ++r)
+            off[r] = bin_of_phase(f0 + (unsigned long long)r * p0.y, M) * T8 + (unsigned)r * MT8;
+        }
+        A2 aw = sAW[0];
+        ulonglong2 pdn = sPD[cnt > 1 ? 1 : 0];
+        A2 awn = sAW[cnt > 1 ? 1 : 0];
+        for (int i = 0; i < cnt; ++i) {
+          const int i2 = (i + 2 < cnt) ? i + 2 : cnt - 1;
+          const ulonglong2 pdnn = sPD[i2];
+          const A2 awnn = sAW[i2];
+          A2 v[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = *reinterpret_cast<const A2*>(my_bins + off[r]);
+          for (int r = 0; r < R; ++r) v[r] = *reinterpret_cast<const A2*>(my_bins + off[r]);
+          const unsigned long long fn = pdn.x + (unsigned long long)j0 * pdn.y;
+          unsigned offn[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) *reinterpret_cast<A2*>(my_bins + off[r]) = acc_add(v[r], aw);
-        pd = pdn;
-        aw = awn;
+          for (int r = 0; r < R; ++r)
+            offn[r] = bin_of_phase(fn + (unsigned long long)r * pdn.y, M) * T8 + (unsigned)r * MT8;
+#pragma unroll
+          for (int r = 0; r < R; ++r) *reinterpret_cast<A2*>(my_bins + off[r]) = acc_add(v[r], aw);
+#pragma unroll
+          for (int r = 0; r < R; ++r) off[r] = offn[r];
+          aw = awn;
+          pdn = pdnn;
+          awn = awnn;
+        }
+      } else {
+        ulonglong2 pd = sPD[0];
+        A2 aw = sAW[0];
+#pragma unroll 2
+        for (int i = 0; i < cnt; ++i) {
+          const int in = (i + 1 < cnt) ? i + 1 : i;
+          const ulonglong2 pdn = sPD[in];
+          const A2 awn = sAW[in];
+          // the R phases are independent multiply-adds (no serial chain of 64-bit adds)
+          const unsigned long long phi0 = pd.x + (unsigned long long)j0 * pd.y;
+          unsigned off[R];
+#pragma unroll
+          for (int r = 0; r < R; ++r)
+            off[r] = bin_of_phase(phi0 + (unsigned long long)r * pd.y, M) * T8 + (unsigned)r * MT8;
+          A2 v[R];
+#pragma unroll
+          for (int r = 0; r < R; ++r) v[r] = *reinterpret_cast<const A2*>(my_bins + off[r]);
+#pragma unroll
+          for (int r = 0; r < R; ++r) *reinterpret_cast<A2*>(my_bins + off[r]) = acc_add(v[r], aw);
+          pd = pdn;
+          aw = awn;
+        }
       }
     } else if (lin) {  // FPW_PHASE_FP32: FP32 phase from an FP32 anchor every K frequencies
       const int K = args.K;
