@@ -45,20 +45,27 @@ constexpr int kShObs = 32;                      // observations per chunk
 constexpr int kShK = 2 * kShObs;                // K entries per chunk (hi, lo)
 constexpr int kShKSteps = kShK / 16;            // MMA k-steps per chunk
 constexpr int kShChunkBytes = kShRows * kShK * 2;  // V image of one chunk: 16 KB
-constexpr int kShThreads = 256;
+constexpr int kShThreads = 512;
 constexpr int kShNMax = 256;                    // MMA N limit (M = 128)
+constexpr int kShMaxFpm = 64;                   // frequencies per accumulator, at most
 constexpr int kShHOperandMax = kShNMax * kShK * 2;   // one H operand of a chunk: 32 KB
 constexpr int kShHSlotBytes = 2 * kShHOperandMax;    // two H operands (two accumulators)
 constexpr int kShTmemCols = 512;
 constexpr unsigned kOneOne = 0x3C003C00u;       // two fp16 1.0
 constexpr long long kWaitClocks = 4000000000LL; // ~2 s at 2 GHz
+constexpr int kMaxPassFreqs = 2 * kShMaxFpm;
+constexpr int kMaxPairs = kMaxPassFreqs * kShObs;
+constexpr int kShVSlots = 4;                    // V chunks in flight: loads run two chunks ahead
+constexpr int kShStage = 1024;                  // observations staged at a time (t, anchor P, step D)
+constexpr int kShStageChunks = kShStage / kShObs;
 
 // Shared-memory carve-up (bytes).
-constexpr int kOffV = 0;                                   // 2 x 16 KB
-constexpr int kOffH = kOffV + 2 * kShChunkBytes;           // 2 x 64 KB
-constexpr int kOffBins = kOffH + 2 * kShHSlotBytes;        // bins of the chunk: [pass freq][32] bytes
-constexpr int kMaxPassFreqs = 2 * kShNMax;                 // M = 1: 256 frequencies per accumulator
-constexpr int kOffBar = kOffBins + kMaxPassFreqs * kShObs;
+constexpr int kOffV = 0;                                   // V chunks: 4 x 16 KB
+constexpr int kOffH = kOffV + kShVSlots * kShChunkBytes;   // H chunks: 2 x 64 KB
+constexpr int kOffOld = kOffH + 2 * kShHSlotBytes;         // bin of every (frequency, observation) pair in H, per slot
+constexpr int kOffF = kOffOld + 2 * kMaxPairs;             // the pass's frequencies (binary64)
+constexpr int kOffStage = kOffF + kMaxPassFreqs * 8;       // t, P, D of kShStage observations
+constexpr int kOffBar = kOffStage + 3 * kShStage * 8;
 constexpr int kSmemBytes = kOffBar + 64;
 
 // Byte offset of element (row r, k-entry q) of a K-major, unswizzled operand
@@ -126,10 +133,15 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
-               : "r"(taddr));
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
+        "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+        "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
@@ -218,30 +230,65 @@ __global__ void __launch_bounds__(256) shared_prep_kernel(const SharedArgs a) {
       if (!isfinite(a.freqs[q])) atomicOr(a.status, kStatusGrid);
 }
 
+// ---------------------------------------------------------------- phase steps
+// Per observation: the 64-bit phase step D_i = frac(t_i df) for the grid's
+// mean spacing df, and max |t| (for the grid-linearity bound).
+__global__ void shared_steps_kernel(const SharedArgs a) {
+  const int64_t F = a.nfreq;
+  const double df = (F > 1) ? (a.freqs[F - 1] - a.freqs[0]) / (double)(F - 1) : 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double t = a.t[i];
+    const bool ok = isfinite(t) && isfinite(df);
+    a.step[i] = ok ? phase_fixed64(t, df) : 0ull;
+    if (ok) atomicMax(a.tmax_bits, (unsigned long long)__double_as_longlong(fabs(t)));
+  }
+}
+
 // ---------------------------------------------------------------- MMA kernel
+// Per chunk of 32 observations (H double-buffered, slot s = chunk & 1; V in
+// four slots, loaded two chunks ahead):
+//   1. wait for the MMAs of chunk - 2 (they read H slot s and the V slot that
+//      chunk + 2 is loaded into), then start that load;
+//   2. each (frequency, observation) pair of the pass clears its previous one
+//      in H slot s and sets its new one (pairs own disjoint 4-byte words);
+//      phases step from the staged anchors (Phi = P_i + j D_i) when the pass's
+//      frequencies lie on the linear grid, else come from exact anchors per pair;
+//   3. one thread waits for the chunk's V (bulk copy), issues the 2 x 4 MMAs
+//      and commits them to the H slot's mbarrier.
+// t and D are staged once per kShStage observations (once per CTA when the
+// curves have at most kShStage observations); P once per (item, block).
 __global__ void __launch_bounds__(kShThreads, 1) shared_mma_kernel(const SharedArgs a) {
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* sV = smem + kOffV;
   unsigned char* sH = smem + kOffH;
-  uint8_t* sBins = smem + kOffBins;
+  uint8_t* sOld = smem + kOffOld;
+  double* sF = reinterpret_cast<double*>(smem + kOffF);
+  double* sT = reinterpret_cast<double*>(smem + kOffStage);
+  unsigned long long* sP = reinterpret_cast<unsigned long long*>(sT + kShStage);
+  unsigned long long* sD = sP + kShStage;
   uint64_t* bar_mma = reinterpret_cast<uint64_t*>(smem + kOffBar);  // [2]
-  uint64_t* bar_v = bar_mma + 2;                                     // [2]
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar_mma + 4);
-  int* s_abort = reinterpret_cast<int*>(tslot + 1);
+  uint64_t* bar_v = bar_mma + 2;                                     // [kShVSlots]
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar_v + kShVSlots);
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int M = a.M, fpm = a.fpm, Nm = a.n_mma, FP = 2 * fpm, rows_used = fpm * M;
+  const int npairs = FP * kShObs;
   const int64_t F = a.nfreq, n = a.n, nch = a.nchunks;
+  const bool resident = n <= kShStage;
   const bool grid_bad = (*(volatile unsigned*)a.status & kStatusGrid) != 0u;
   const int64_t items = grid_bad ? 0 : a.ngroups * a.npass;
   const float cal = (float)a.inv_alpha2;
+  const double df = (F > 1) ? (a.freqs[F - 1] - a.freqs[0]) / (double)(F - 1) : 0.0;
+  const double tmax = __longlong_as_double((long long)*a.tmax_bits);
+  const uint32_t op_bytes = (uint32_t)(Nm * kShK * 2);  // one H operand
+  // byte offset of this lane's observation (hi, lo) word inside a row of H
+  const uint32_t lane_off = (uint32_t)(lane >> 3) * (uint32_t)(Nm * 32) + (uint32_t)((lane >> 2) & 1) * 128u +
+                            (uint32_t)(lane & 3) * 4u;
 
   if (tid == 0) {
     mbar_init(&bar_mma[0]);
     mbar_init(&bar_mma[1]);
-    mbar_init(&bar_v[0]);
-    mbar_init(&bar_v[1]);
-    *s_abort = 0;
+    for (int v = 0; v < kShVSlots; ++v) mbar_init(&bar_v[v]);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -250,9 +297,20 @@ __global__ void __launch_bounds__(kShThreads, 1) shared_mma_kernel(const SharedA
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  // H rows beyond fpm * M (padding up to the MMA's N) stay zero for good
+  // H starts as all pairs in bin 0 (rows beyond fpm * M stay zero for good)
   for (int e = tid; e < 2 * kShHSlotBytes / 16; e += kShThreads)
     reinterpret_cast<uint4*>(sH)[e] = make_uint4(0u, 0u, 0u, 0u);
+  __syncthreads();
+  for (int e = tid; e < npairs; e += kShThreads) {
+    const int j = e >> 5;
+    const int op = j >= fpm ? 1 : 0;
+    const uint32_t r = (uint32_t)((j - op * fpm) * M);
+    const uint32_t w = lane_off + (uint32_t)op * op_bytes + (r >> 3) * 256u + (r & 7u) * 16u;
+    for (int s = 0; s < 2; ++s) {
+      *reinterpret_cast<uint32_t*>(sH + s * kShHSlotBytes + w) = kOneOne;
+      sOld[s * kMaxPairs + e] = 0;
+    }
+  }
   fence_async_smem();
   fence_before_sync();
   __syncthreads();
@@ -260,37 +318,46 @@ __global__ void __launch_bounds__(kShThreads, 1) shared_mma_kernel(const SharedA
   const uint32_t tmem = *tslot;
   const uint32_t idesc = mma_idesc(kShRows, Nm);
 
-  // this thread's H rows (at most two: rows_used <= 2 x 256 over 256 threads... per operand)
-  // row id e in [0, 2 * rows_used): operand e / rows_used, (j, m) within it
-  int my_row_j[2], my_row_m[2];
-  uint32_t my_row_off[2];
-#pragma unroll
-  for (int kk = 0; kk < 2; ++kk) {
-    const int e = tid + kk * kShThreads;
-    my_row_j[kk] = -1;
-    my_row_m[kk] = 0;
-    my_row_off[kk] = 0;
-    if (e < 2 * rows_used) {
-      const int op = e / rows_used, r = e % rows_used;
-      my_row_j[kk] = op * fpm + r / M;  // pass-local frequency
-      my_row_m[kk] = r % M;
-      my_row_off[kk] = (uint32_t)(op * (Nm * kShK * 2)) + (uint32_t)(r >> 3) * 256u + (uint32_t)(r & 7) * 16u;
-    }
-  }
-
-  uint32_t ph_mma[2] = {0u, 0u}, ph_v[2] = {0u, 0u};
+  uint32_t ph_mma[2] = {0u, 0u}, ph_v[kShVSlots] = {0u, 0u, 0u, 0u};
   bool pend[2] = {false, false};
-  bool abort = false;
+  bool fail = false, abort = false, staged = false;
+
+  // the first item's first two V chunks
+  if (tid == 0 && (int64_t)blockIdx.x < items) {
+    const unsigned char* img = a.image + (size_t)(blockIdx.x / a.npass) * (size_t)nch * kShChunkBytes;
+    for (int64_t c = 0; c < 2 && c < nch; ++c)
+      bulk_load(sV + c * kShChunkBytes, img + (size_t)c * kShChunkBytes, kShChunkBytes, &bar_v[c]);
+  }
 
   for (int64_t item = blockIdx.x; item < items && !abort; item += gridDim.x) {
     const int64_t g = item / a.npass, p = item % a.npass;
     const int64_t f0 = p * FP;
+    const double fa = a.freqs[f0];
     const unsigned char* img = a.image + (size_t)g * (size_t)nch * kShChunkBytes;
+    bool nonlin = false;
+    for (int j = tid; j < FP; j += kShThreads) {
+      const int64_t fi = f0 + j;
+      const double f = fi < F ? a.freqs[fi] : 0.0;
+      sF[j] = f;
+      if (fi < F && fabs(f - fma((double)j, df, fa)) * tmax > kGridTolCycles) nonlin = true;
+    }
+    const bool lin = !__syncthreads_or(nonlin);
     for (int64_t ch = 0; ch < nch; ++ch) {
-      const int s = (int)(ch & 1);
-      bool fail = false;
-      if (pend[s]) {  // the MMAs of chunk ch - 2 read this buffer
-        fail = !mbar_wait(&bar_mma[s], ph_mma[s]);
+      const int s = (int)(ch & 1), vs = (int)(ch & (kShVSlots - 1));
+      if (ch % kShStageChunks == 0) {  // stage the next block of observations (same thread per entry throughout)
+        const int64_t o0 = ch * kShObs;
+        for (int i = tid; i < kShStage; i += kShThreads) {
+          const int64_t oi = o0 + i;
+          if (!resident || !staged) {
+            sT[i] = oi < n ? a.t[oi] : 0.0;
+            sD[i] = oi < n ? a.step[oi] : 0ull;
+          }
+          sP[i] = phase_fixed64(sT[i], fa);
+        }
+        staged = true;
+      }
+      if (pend[s]) {  // MMAs of chunk ch - 2 read H slot s and V slot (ch + 2) & 3
+        fail |= !mbar_wait(&bar_mma[s], ph_mma[s]);
         ph_mma[s] ^= 1u;
         pend[s] = false;
       }
@@ -298,67 +365,54 @@ __global__ void __launch_bounds__(kShThreads, 1) shared_mma_kernel(const SharedA
         abort = true;
         break;
       }
-      if (tid == 0) bulk_load(sV + s * kShChunkBytes, img + (size_t)ch * kShChunkBytes, kShChunkBytes, &bar_v[s]);
-      // bins of the chunk: pair (j, i) -> sBins[j * 32 + i]
-      for (int e = tid; e < FP * kShObs; e += kShThreads) {
-        const int j = e / kShObs, i = e % kShObs;
-        const int64_t fi = f0 + j, oi = ch * kShObs + i;
-        unsigned m = 0u;
-        if (fi < F && oi < n) m = bin_of_phase(phase_fixed64(a.t[oi], a.freqs[fi]), (unsigned)M);
-        sBins[e] = (uint8_t)m;
+      if (tid == 0 && ch + 2 < nch) {
+        const int v2 = (int)((ch + 2) & (kShVSlots - 1));
+        bulk_load(sV + v2 * kShChunkBytes, img + (size_t)(ch + 2) * kShChunkBytes, kShChunkBytes, &bar_v[v2]);
       }
-      __syncthreads();
-      // one-hot H: 16-byte pieces (4 observations x hi/lo) per (row, k-group)
       unsigned char* hs = sH + s * kShHSlotBytes;
-#pragma unroll
-      for (int kk = 0; kk < 2; ++kk) {
-        if (my_row_j[kk] < 0) continue;
-        const uint32_t mrep = (uint32_t)my_row_m[kk] * 0x01010101u;
-        const uint32_t* bw = reinterpret_cast<const uint32_t*>(sBins + my_row_j[kk] * kShObs);
-#pragma unroll
-        for (int q4 = 0; q4 < kShObs / 4; ++q4) {
-          const uint32_t eq = __vcmpeq4(bw[q4], mrep);
-          uint4 v;
-          v.x = __byte_perm(eq, 0u, 0x0000u) & kOneOne;
-          v.y = __byte_perm(eq, 0u, 0x1111u) & kOneOne;
-          v.z = __byte_perm(eq, 0u, 0x2222u) & kOneOne;
-          v.w = __byte_perm(eq, 0u, 0x3333u) & kOneOne;
-          const uint32_t off = my_row_off[kk] + (uint32_t)(q4 >> 1) * (uint32_t)(Nm * 32) + (uint32_t)(q4 & 1) * 128u;
-          *reinterpret_cast<uint4*>(hs + off) = v;
-        }
+      uint8_t* old = sOld + s * kMaxPairs;
+      const int ib = (int)(ch % kShStageChunks) * kShObs + lane;
+      const bool obs_ok = ch * kShObs + lane < n;
+      const unsigned long long P = sP[ib], D = sD[ib];
+      const double tl = sT[ib];
+      for (int e = tid; e < npairs; e += kShThreads) {
+        const int j = e >> 5;  // warp-uniform
+        const int op = j >= fpm ? 1 : 0;
+        const int jl = j - op * fpm;
+        unsigned m = 0u;
+        if (obs_ok && f0 + j < F)
+          m = bin_of_phase(lin ? P + (unsigned long long)j * D : phase_fixed64(tl, sF[j]), (unsigned)M);
+        const uint32_t base = lane_off + (uint32_t)op * op_bytes;
+        const uint32_t ro = (uint32_t)(jl * M) + old[e];
+        const uint32_t rn = (uint32_t)(jl * M) + m;
+        *reinterpret_cast<uint32_t*>(hs + base + (ro >> 3) * 256u + (ro & 7u) * 16u) = 0u;
+        *reinterpret_cast<uint32_t*>(hs + base + (rn >> 3) * 256u + (rn & 7u) * 16u) = kOneOne;
+        old[e] = (uint8_t)m;
       }
       fence_async_smem();
       __syncthreads();
       if (tid == 0) {
-        if (!mbar_wait(&bar_v[s], ph_v[s])) {
-          atomicOr(a.status, kStatusTimeout);
-          *s_abort = 1;
+        if (!mbar_wait(&bar_v[vs], ph_v[vs])) {
+          fail = true;
         } else {
           fence_after_sync();
-          const uint32_t va = smem_addr(sV + s * kShChunkBytes), ha = smem_addr(hs);
+          const uint32_t va = smem_addr(sV + vs * kShChunkBytes), ha = smem_addr(hs);
 #pragma unroll
           for (int ks = 0; ks < kShKSteps; ++ks) {
             const uint64_t dv = smem_desc(va + (uint32_t)ks * (kShRows * 32u));
             const uint32_t acc = (ch > 0 || ks > 0) ? 1u : 0u;
 #pragma unroll
-            for (int op = 0; op < 2; ++op) {
-              const uint64_t dh = smem_desc(ha + (uint32_t)op * (uint32_t)(Nm * kShK * 2) + (uint32_t)ks * (uint32_t)(Nm * 32));
-              mma_f16(tmem + (uint32_t)op * 256u, dv, dh, idesc, acc);
-            }
+            for (int op = 0; op < 2; ++op)
+              mma_f16(tmem + (uint32_t)op * 256u, dv,
+                      smem_desc(ha + (uint32_t)op * op_bytes + (uint32_t)ks * (uint32_t)(Nm * 32)), idesc, acc);
           }
           mma_commit(&bar_mma[s]);
         }
       }
-      ph_v[s] ^= 1u;
+      ph_v[vs] ^= 1u;
       pend[s] = true;
-      __syncthreads();
-      if (*s_abort) {
-        abort = true;
-        break;
-      }
     }
     // drain this item's MMAs
-    bool fail = false;
     for (int s = 0; s < 2; ++s)
       if (pend[s]) {
         fail |= !mbar_wait(&bar_mma[s], ph_mma[s]);
@@ -368,46 +422,56 @@ __global__ void __launch_bounds__(kShThreads, 1) shared_mma_kernel(const SharedA
     if (__syncthreads_or(fail)) abort = true;
     if (abort) break;
     fence_after_sync();
+    // the next item's first two V chunks load during this epilogue
+    const int64_t next = item + gridDim.x;
+    if (tid == 0 && next < items) {
+      const unsigned char* img2 = a.image + (size_t)(next / a.npass) * (size_t)nch * kShChunkBytes;
+      for (int64_t c = 0; c < 2 && c < nch; ++c)
+        bulk_load(sV + c * kShChunkBytes, img2 + (size_t)c * kShChunkBytes, kShChunkBytes, &bar_v[c]);
+    }
 
-    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 of accumulator w / 4
-    const int quarter = warp & 3, op = warp >> 2;
-    const int row = quarter * 32 + lane;
-    const int64_t c = g * kShCurves + (row >> 1);
-    const bool even = (row & 1) == 0;
-    const bool cvalid = c < a.ncurves;
-    const float sa = cvalid ? a.inv_scale[2 * c] : 0.f, sw = cvalid ? a.inv_scale[2 * c + 1] : 0.f;
-    const bool cbad = cvalid && a.curve_bad[c];
-    float acc = 0.f;
-    int m = 0, jl = 0;
-    const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)op * 256u;
-    for (int c0 = 0; c0 < rows_used; c0 += 8) {
-      uint32_t v[8];
-      if (nch > 0) {
-        tmem_ld8(tbase + (uint32_t)c0, v);
-      } else {
+    // epilogue (warps 0-7): warp w reads TMEM lanes 32 (w % 4) .. + 31 of accumulator w / 4
+    if (warp < 8) {
+      const int quarter = warp & 3, op = warp >> 2;
+      const int row = quarter * 32 + lane;
+      const int64_t c = g * kShCurves + (row >> 1);
+      const bool even = (row & 1) == 0;
+      const bool cvalid = c < a.ncurves;
+      const float sa = cvalid ? a.inv_scale[2 * c] : 0.f, sw = cvalid ? a.inv_scale[2 * c + 1] : 0.f;
+      const bool cbad = cvalid && a.curve_bad[c];
+      float acc = 0.f;
+      int m = 0, jl = 0;
+      const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)op * 256u;
+      for (int c0 = 0; c0 < rows_used; c0 += 32) {
+        uint32_t v[32];
+        if (nch > 0) {
+          tmem_ld32(tbase + (uint32_t)c0, v);
+        } else {
 #pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = 0u;
-      }
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        if (c0 + u >= rows_used) break;
-        const float val = __uint_as_float(v[u]);
-        const float other = __shfl_xor_sync(0xffffffffu, val, 1);
-        if (even) {
-          const float A = val * sa, B = other * sw;
-          const float den = B + cal;
-          acc += den > 0.f ? (A * A) / den : 0.f;
+          for (int u = 0; u < 32; ++u) v[u] = 0u;
         }
-        if (++m == M) {
-          const int64_t fi = f0 + (int64_t)op * fpm + jl;
-          if (even && cvalid && fi < F) {
-            const float S = cbad ? __int_as_float(0x7fc00000) : acc;
-            if (a.S32) a.S32[c * F + fi] = S;
-            if (a.S_out) a.S_out[c * F + fi] = (double)S;
+#pragma unroll
+        for (int u = 0; u < 32; ++u) {
+          if (c0 + u < rows_used) {
+            const float val = __uint_as_float(v[u]);
+            const float other = __shfl_xor_sync(0xffffffffu, val, 1);
+            if (even) {
+              const float A = val * sa, B = other * sw;
+              const float den = B + cal;
+              acc += den > 0.f ? (A * A) / den : 0.f;
+            }
+            if (++m == M) {
+              const int64_t fi = f0 + (int64_t)op * fpm + jl;
+              if (even && cvalid && fi < F) {
+                const float S = cbad ? __int_as_float(0x7fc00000) : acc;
+                if (a.S32) a.S32[c * F + fi] = S;
+                if (a.S_out) a.S_out[c * F + fi] = (double)S;
+              }
+              acc = 0.f;
+              m = 0;
+              ++jl;
+            }
           }
-          acc = 0.f;
-          m = 0;
-          ++jl;
         }
       }
     }
@@ -415,12 +479,15 @@ __global__ void __launch_bounds__(kShThreads, 1) shared_mma_kernel(const SharedA
     __syncthreads();
   }
   // teardown: nothing of this CTA may still be in flight when TMEM is freed
+  // (MMAs; and V loads issued for an item that was not started)
   for (int s = 0; s < 2; ++s)
     if (pend[s]) {
-      if (!mbar_wait(&bar_mma[s], ph_mma[s])) atomicOr(a.status, kStatusTimeout);
+      if (!mbar_wait(&bar_mma[s], ph_mma[s])) fail = true;
       pend[s] = false;
     }
-  if (abort && tid == 0) atomicOr(a.status, kStatusTimeout);
+  if (abort || fail) {
+    if (fail) atomicOr(a.status, kStatusTimeout);
+  }
   fence_before_sync();
   __syncthreads();
   if (warp == 0)
@@ -525,7 +592,7 @@ int shared_curves_per_group() { return kShCurves; }
 // Frequencies per accumulator and the MMA's N for M bins (0 if M is too large).
 int shared_freqs_per_mma(int M, int* n_mma) {
   if (M < 1 || M > kShNMax) return 0;
-  const int fpm = kShNMax / M;
+  const int fpm = kShNMax / M < kShMaxFpm ? kShNMax / M : kShMaxFpm;
   *n_mma = ((fpm * M + 15) / 16) * 16;
   return fpm;
 }
@@ -542,6 +609,14 @@ cudaError_t launch_shared(const SharedArgs& a, int nsm, cudaStream_t st) {
   shared_prep_kernel<<<(unsigned)slots, 256, 0, st>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(a.tmax_bits, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  if (a.n > 0) {
+    const int64_t blocks = (a.n + 255) / 256;
+    shared_steps_kernel<<<(unsigned)(blocks < 1024 ? blocks : 1024), 256, 0, st>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   const int64_t items = a.ngroups * a.npass;
   if (items > 0) {
     const int grid = (int)(items < nsm ? items : nsm);

@@ -22,6 +22,8 @@ struct SharedArgs {
   int64_t nchunks;          // chunks of 32 observations
   unsigned char* image;     // fp16 hi/lo operand image [ngroups][nchunks][16 KB]
   float* inv_scale;         // [ngroups * 64][2]: 2^-e for a and w
+  unsigned long long* step; // [n] 64-bit phase step frac(t_i df) of the grid's mean spacing df
+  unsigned long long* tmax_bits;  // max |t| (binary64 bits)
   uint8_t* curve_bad;       // [ngroups * 64]
   unsigned* status;
   double inv_alpha2;
