@@ -66,7 +66,7 @@ constexpr int kOffOld = kOffH + 2 * kShHSlotBytes;         // bin of every (freq
 constexpr int kOffF = kOffOld + 2 * kMaxPairs;             // the pass's frequencies (binary64)
 constexpr int kOffStage = kOffF + kMaxPassFreqs * 8;       // t, P, D of kShStage observations
 constexpr int kOffBar = kOffStage + 3 * kShStage * 8;
-constexpr int kSmemBytes = kOffBar + 64;
+constexpr int kSmemBytes = kOffBar + 128;
 
 // Byte offset of element (row r, k-entry q) of a K-major, unswizzled operand
 // with R rows and kShK columns: one 16-column k-step after another; inside a
@@ -93,10 +93,6 @@ __device__ __forceinline__ uint32_t mma_idesc(int M, int N) {
   return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ void mbar_init(uint64_t* bar) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
-}
-
 // Bounded wait for completion of phase `parity` of an mbarrier.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   const long long t0 = clock64();
@@ -110,6 +106,44 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     if (done) return true;
     if (clock64() - t0 > kWaitClocks) return false;
   }
+}
+
+// mbarrier wait that also gives up when another role of the CTA set *abort.
+__device__ __forceinline__ bool mbar_wait_ab(uint64_t* bar, uint32_t parity, volatile int* abort) {
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (*abort || clock64() - t0 > kWaitClocks) return false;
+  }
+}
+
+__device__ __forceinline__ void mbar_init_n(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// Named barrier among the builder warps only (the issuer warp never joins).
+__device__ __forceinline__ void builders_sync(int nthreads) {
+  asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+}
+
+__device__ __forceinline__ bool builders_or(bool v, int nthreads) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.or.pred q, 1, %2, p;\n\tselp.u32 %0, 1, 0, q;\n\t}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v), "r"(nthreads)
+      : "memory");
+  return r != 0u;
 }
 
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
@@ -245,18 +279,25 @@ __global__ void shared_steps_kernel(const SharedArgs a) {
 }
 
 // ---------------------------------------------------------------- MMA kernel
-// Per chunk of 32 observations (H double-buffered, slot s = chunk & 1; V in
-// four slots, loaded two chunks ahead):
-//   1. wait for the MMAs of chunk - 2 (they read H slot s and the V slot that
-//      chunk + 2 is loaded into), then start that load;
-//   2. each (frequency, observation) pair of the pass clears its previous one
-//      in H slot s and sets its new one (pairs own disjoint 4-byte words);
-//      phases step from the staged anchors (Phi = P_i + j D_i) when the pass's
-//      frequencies lie on the linear grid, else come from exact anchors per pair;
-//   3. one thread waits for the chunk's V (bulk copy), issues the 2 x 4 MMAs
-//      and commits them to the H slot's mbarrier.
-// t and D are staged once per kShStage observations (once per CTA when the
-// curves have at most kShStage observations); P once per (item, block).
+// Warp-specialised pipeline over this CTA's stream of chunks (32 observations
+// of one item each; gc counts them across items):
+//  * builder warps (0-14): for chunk gc, wait until the MMAs of gc - 2 have
+//    released H slot gc & 1 (mbarrier `empty`), then each (frequency,
+//    observation) pair clears its previous one in that slot and sets its new
+//    one (pairs own disjoint 4-byte words; phases step from staged anchors,
+//    Phi = P_i + j D_i, when the pass lies on the linear grid, else exact
+//    anchors per pair); each warp then arrives on `full`. At an item's end
+//    warps 0-7 read the accumulators (after `acc`) and arrive on `tfree`.
+//  * issuer warp (15, one lane): waits for `full`, starts the bulk copy of the
+//    V chunk two chunks ahead (its slot was last read by the MMAs of gc - 2,
+//    complete once `full` of gc has completed), waits for V of gc (and, on an
+//    item's first chunk, for `tfree`), issues the 2 x 4 MMAs and commits them
+//    to `empty` (and to `acc` after an item's last chunk).
+// No block-wide barrier inside the loop; every wait is bounded and gives up
+// when another role has set the abort flag.
+constexpr int kShBuilderWarps = kShThreads / 32 - 1;
+constexpr int kShBuilders = kShBuilderWarps * 32;
+
 __global__ void __launch_bounds__(kShThreads, 1) shared_mma_kernel(const SharedArgs a) {
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* sV = smem + kOffV;
@@ -266,9 +307,13 @@ __global__ void __launch_bounds__(kShThreads, 1) shared_mma_kernel(const SharedA
   double* sT = reinterpret_cast<double*>(smem + kOffStage);
   unsigned long long* sP = reinterpret_cast<unsigned long long*>(sT + kShStage);
   unsigned long long* sD = sP + kShStage;
-  uint64_t* bar_mma = reinterpret_cast<uint64_t*>(smem + kOffBar);  // [2]
-  uint64_t* bar_v = bar_mma + 2;                                     // [kShVSlots]
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar_v + kShVSlots);
+  uint64_t* bar_full = reinterpret_cast<uint64_t*>(smem + kOffBar);  // [2]
+  uint64_t* bar_empty = bar_full + 2;                                 // [2]
+  uint64_t* bar_v = bar_empty + 2;                                    // [kShVSlots]
+  uint64_t* bar_acc = bar_v + kShVSlots;
+  uint64_t* bar_tfree = bar_acc + 1;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar_tfree + 1);
+  volatile int* s_abort = reinterpret_cast<volatile int*>(tslot + 1);
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int M = a.M, fpm = a.fpm, Nm = a.n_mma, FP = 2 * fpm, rows_used = fpm * M;
@@ -277,6 +322,7 @@ __global__ void __launch_bounds__(kShThreads, 1) shared_mma_kernel(const SharedA
   const bool resident = n <= kShStage;
   const bool grid_bad = (*(volatile unsigned*)a.status & kStatusGrid) != 0u;
   const int64_t items = grid_bad ? 0 : a.ngroups * a.npass;
+  const int64_t my_items = (int64_t)blockIdx.x < items ? (items - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   const float cal = (float)a.inv_alpha2;
   const double df = (F > 1) ? (a.freqs[F - 1] - a.freqs[0]) / (double)(F - 1) : 0.0;
   const double tmax = __longlong_as_double((long long)*a.tmax_bits);
@@ -286,9 +332,14 @@ __global__ void __launch_bounds__(kShThreads, 1) shared_mma_kernel(const SharedA
                             (uint32_t)(lane & 3) * 4u;
 
   if (tid == 0) {
-    mbar_init(&bar_mma[0]);
-    mbar_init(&bar_mma[1]);
-    for (int v = 0; v < kShVSlots; ++v) mbar_init(&bar_v[v]);
+    for (int q = 0; q < 2; ++q) {
+      mbar_init_n(&bar_full[q], kShBuilderWarps);
+      mbar_init_n(&bar_empty[q], 1);
+    }
+    for (int v = 0; v < kShVSlots; ++v) mbar_init_n(&bar_v[v], 1);
+    mbar_init_n(bar_acc, 1);
+    mbar_init_n(bar_tfree, 8);
+    *s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -306,9 +357,9 @@ __global__ void __launch_bounds__(kShThreads, 1) shared_mma_kernel(const SharedA
     const int op = j >= fpm ? 1 : 0;
     const uint32_t r = (uint32_t)((j - op * fpm) * M);
     const uint32_t w = lane_off + (uint32_t)op * op_bytes + (r >> 3) * 256u + (r & 7u) * 16u;
-    for (int s = 0; s < 2; ++s) {
-      *reinterpret_cast<uint32_t*>(sH + s * kShHSlotBytes + w) = kOneOne;
-      sOld[s * kMaxPairs + e] = 0;
+    for (int q = 0; q < 2; ++q) {
+      *reinterpret_cast<uint32_t*>(sH + q * kShHSlotBytes + w) = kOneOne;
+      sOld[q * kMaxPairs + e] = 0;
     }
   }
   fence_async_smem();
@@ -316,178 +367,221 @@ __global__ void __launch_bounds__(kShThreads, 1) shared_mma_kernel(const SharedA
   __syncthreads();
   fence_after_sync();
   const uint32_t tmem = *tslot;
-  const uint32_t idesc = mma_idesc(kShRows, Nm);
+  bool fail = false;
 
-  uint32_t ph_mma[2] = {0u, 0u}, ph_v[kShVSlots] = {0u, 0u, 0u, 0u};
-  bool pend[2] = {false, false};
-  bool fail = false, abort = false, staged = false;
-
-  // the first item's first two V chunks
-  if (tid == 0 && (int64_t)blockIdx.x < items) {
-    const unsigned char* img = a.image + (size_t)(blockIdx.x / a.npass) * (size_t)nch * kShChunkBytes;
-    for (int64_t c = 0; c < 2 && c < nch; ++c)
-      bulk_load(sV + c * kShChunkBytes, img + (size_t)c * kShChunkBytes, kShChunkBytes, &bar_v[c]);
-  }
-
-  for (int64_t item = blockIdx.x; item < items && !abort; item += gridDim.x) {
-    const int64_t g = item / a.npass, p = item % a.npass;
-    const int64_t f0 = p * FP;
-    const double fa = a.freqs[f0];
-    const unsigned char* img = a.image + (size_t)g * (size_t)nch * kShChunkBytes;
-    bool nonlin = false;
-    for (int j = tid; j < FP; j += kShThreads) {
-      const int64_t fi = f0 + j;
-      const double f = fi < F ? a.freqs[fi] : 0.0;
-      sF[j] = f;
-      if (fi < F && fabs(f - fma((double)j, df, fa)) * tmax > kGridTolCycles) nonlin = true;
-    }
-    const bool lin = !__syncthreads_or(nonlin);
-    for (int64_t ch = 0; ch < nch; ++ch) {
-      const int s = (int)(ch & 1), vs = (int)(ch & (kShVSlots - 1));
-      if (ch % kShStageChunks == 0) {  // stage the next block of observations (same thread per entry throughout)
-        const int64_t o0 = ch * kShObs;
-        for (int i = tid; i < kShStage; i += kShThreads) {
-          const int64_t oi = o0 + i;
-          if (!resident || !staged) {
-            sT[i] = oi < n ? a.t[oi] : 0.0;
-            sD[i] = oi < n ? a.step[oi] : 0ull;
-          }
-          sP[i] = phase_fixed64(sT[i], fa);
+  if (warp == kShBuilderWarps) {
+    // ------------------------------------------------------------ issuer
+    if (lane == 0 && my_items > 0 && nch > 0) {
+      const uint32_t idesc = mma_idesc(kShRows, Nm);
+      // descriptors of chunk operands: a base descriptor plus the byte offset / 16
+      // in the start-address field (all offsets stay inside shared memory)
+      const uint64_t dv0 = smem_desc(smem_addr(sV)), dh0 = smem_desc(smem_addr(sH));
+      const int64_t total = my_items * nch;
+      // the V-load cursor (item lk of this CTA, chunk lch) runs two chunks ahead
+      // of the MMA cursor; both advance incrementally (no 64-bit division per chunk)
+      int64_t lk = 0, lch = 0;
+      const unsigned char* limg = a.image + (size_t)(blockIdx.x / a.npass) * (size_t)nch * kShChunkBytes;
+      auto load_next = [&](int slot) {
+        bulk_load(sV + slot * kShChunkBytes, limg + (size_t)lch * kShChunkBytes, kShChunkBytes, &bar_v[slot]);
+        if (++lch == nch) {
+          lch = 0;
+          ++lk;
+          const int64_t it = blockIdx.x + lk * gridDim.x;
+          limg = a.image + (size_t)(it / a.npass) * (size_t)nch * kShChunkBytes;
         }
-        staged = true;
+      };
+      for (int64_t c = 0; c < 2 && c < total; ++c) load_next((int)c);
+      uint32_t ph_full[2] = {0u, 0u}, ph_v[kShVSlots] = {0u, 0u, 0u, 0u}, ph_tfree = 0u;
+      uint32_t commits[2] = {0u, 0u};
+      bool v_out[kShVSlots] = {total > 0, total > 1, false, false};  // a load is in flight in the slot
+      int64_t ch = 0;
+      for (int64_t gc = 0; gc < total && !fail; ++gc, ch = (ch + 1 == nch) ? 0 : ch + 1) {
+        const int s = (int)(gc & 1), vs = (int)(gc & (kShVSlots - 1));
+        if (!mbar_wait_ab(&bar_full[s], ph_full[s], s_abort)) { fail = true; break; }
+        ph_full[s] ^= 1u;
+        if (gc + 2 < total) {  // its slot was last read by the MMAs of gc - 2, done before `full` of gc
+          const int v2 = (int)((gc + 2) & (kShVSlots - 1));
+          load_next(v2);
+          v_out[v2] = true;
+        }
+        if (!mbar_wait_ab(&bar_v[vs], ph_v[vs], s_abort)) { fail = true; break; }
+        ph_v[vs] ^= 1u;
+        v_out[vs] = false;
+        if (ch == 0 && gc > 0) {  // the previous item's accumulators have been read
+          if (!mbar_wait_ab(bar_tfree, ph_tfree, s_abort)) { fail = true; break; }
+          ph_tfree ^= 1u;
+        }
+        fence_after_sync();
+        const uint64_t dvs = dv0 + (uint64_t)((vs * kShChunkBytes) >> 4);
+        const uint64_t dhs = dh0 + (uint64_t)((s * kShHSlotBytes) >> 4);
+#pragma unroll
+        for (int ks = 0; ks < kShKSteps; ++ks) {
+          const uint32_t acc = (ch > 0 || ks > 0) ? 1u : 0u;
+          const uint64_t dvk = dvs + (uint64_t)((ks * kShRows * 32) >> 4);
+          const uint64_t dhk = dhs + (uint64_t)(((uint32_t)ks * (uint32_t)(Nm * 32)) >> 4);
+          mma_f16(tmem, dvk, dhk, idesc, acc);
+          mma_f16(tmem + 256u, dvk, dhk + (uint64_t)(op_bytes >> 4), idesc, acc);
+        }
+        mma_commit(&bar_empty[s]);
+        ++commits[s];
+        if (ch == nch - 1) mma_commit(bar_acc);
       }
-      if (pend[s]) {  // MMAs of chunk ch - 2 read H slot s and V slot (ch + 2) & 3
-        fail |= !mbar_wait(&bar_mma[s], ph_mma[s]);
-        ph_mma[s] ^= 1u;
-        pend[s] = false;
+      if (fail) {
+        *s_abort = 1;
+        atomicOr(a.status, kStatusTimeout);
+        // nothing may be in flight when the CTA frees TMEM and exits: bounded
+        // waits for the last commit of each slot and for outstanding V loads
+        for (int q = 0; q < 2; ++q)
+          if (commits[q] > 0u) mbar_wait(&bar_empty[q], (commits[q] - 1u) & 1u);
+        for (int v = 0; v < kShVSlots; ++v)
+          if (v_out[v]) mbar_wait(&bar_v[v], ph_v[v]);
       }
-      if (__syncthreads_or(fail)) {
-        abort = true;
-        break;
+    }
+  } else {
+    // ------------------------------------------------------------ builders (+ epilogue in warps 0-7)
+    // Every builder runs the same loops to the end and passes every named
+    // barrier even after a failure (it then skips the work), so no builder
+    // can wait at a barrier for one that left; failure decisions are made
+    // warp-uniform before any warp-collective instruction.
+    uint32_t ph_empty[2] = {0u, 0u}, ph_acc = 0u;
+    bool staged = false;
+    int64_t gc = 0;
+    for (int64_t k = 0; k < my_items; ++k) {
+      const int64_t item = blockIdx.x + k * gridDim.x;
+      const int64_t g = item / a.npass, p = item % a.npass;
+      const int64_t f0 = p * FP;
+      const double fa = a.freqs[f0];
+      if (k > 0) builders_sync(kShBuilders);  // every builder is done with the previous item's sF and stage
+      bool nonlin = false;
+      for (int j = tid; j < FP; j += kShBuilders) {
+        const int64_t fi = f0 + j;
+        const double f = fi < F ? a.freqs[fi] : 0.0;
+        sF[j] = f;
+        if (fi < F && fabs(f - fma((double)j, df, fa)) * tmax > kGridTolCycles) nonlin = true;
       }
-      if (tid == 0 && ch + 2 < nch) {
-        const int v2 = (int)((ch + 2) & (kShVSlots - 1));
-        bulk_load(sV + v2 * kShChunkBytes, img + (size_t)(ch + 2) * kShChunkBytes, kShChunkBytes, &bar_v[v2]);
+      const bool lin = !builders_or(nonlin, kShBuilders);
+      for (int64_t ch = 0; ch < nch; ++ch, ++gc) {
+        const int s = (int)(gc & 1);
+        if (ch % kShStageChunks == 0) {  // stage a block of observations (same thread per entry throughout)
+          if (ch > 0) builders_sync(kShBuilders);
+          const int64_t o0 = ch * kShObs;
+          for (int i = tid; i < kShStage; i += kShBuilders) {
+            const int64_t oi = o0 + i;
+            if (!resident || !staged) {
+              sT[i] = oi < n ? a.t[oi] : 0.0;
+              sD[i] = oi < n ? a.step[oi] : 0ull;
+            }
+            sP[i] = phase_fixed64(sT[i], fa);
+          }
+          staged = true;
+          builders_sync(kShBuilders);
+        }
+        if (!fail && gc >= 2) {  // the MMAs of gc - 2 read H slot s
+          fail = !mbar_wait_ab(&bar_empty[s], ph_empty[s], s_abort);
+          ph_empty[s] ^= 1u;
+        }
+        fail = __any_sync(0xffffffffu, fail);
+        if (fail && lane == 0) *s_abort = 1;  // the other roles stop waiting
+        if (!fail) {
+          unsigned char* hs = sH + s * kShHSlotBytes;
+          uint8_t* old = sOld + s * kMaxPairs;
+          const int ib = (int)(ch % kShStageChunks) * kShObs + lane;
+          const bool obs_ok = ch * kShObs + lane < n;
+          const unsigned long long P = sP[ib], D = sD[ib];
+          const double tl = sT[ib];
+          for (int e = tid; e < npairs; e += kShBuilders) {
+            const int j = e >> 5;  // warp-uniform
+            const int op = j >= fpm ? 1 : 0;
+            const int jl = j - op * fpm;
+            unsigned m = 0u;
+            if (obs_ok && f0 + j < F)
+              m = bin_of_phase(lin ? P + (unsigned long long)j * D : phase_fixed64(tl, sF[j]), (unsigned)M);
+            const uint32_t base = lane_off + (uint32_t)op * op_bytes;
+            const uint32_t ro = (uint32_t)(jl * M) + old[e];
+            const uint32_t rn = (uint32_t)(jl * M) + m;
+            *reinterpret_cast<uint32_t*>(hs + base + (ro >> 3) * 256u + (ro & 7u) * 16u) = 0u;
+            *reinterpret_cast<uint32_t*>(hs + base + (rn >> 3) * 256u + (rn & 7u) * 16u) = kOneOne;
+            old[e] = (uint8_t)m;
+          }
+          fence_async_smem();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&bar_full[s]);
+        }
       }
-      unsigned char* hs = sH + s * kShHSlotBytes;
-      uint8_t* old = sOld + s * kMaxPairs;
-      const int ib = (int)(ch % kShStageChunks) * kShObs + lane;
-      const bool obs_ok = ch * kShObs + lane < n;
-      const unsigned long long P = sP[ib], D = sD[ib];
-      const double tl = sT[ib];
-      for (int e = tid; e < npairs; e += kShThreads) {
-        const int j = e >> 5;  // warp-uniform
-        const int op = j >= fpm ? 1 : 0;
-        const int jl = j - op * fpm;
-        unsigned m = 0u;
-        if (obs_ok && f0 + j < F)
-          m = bin_of_phase(lin ? P + (unsigned long long)j * D : phase_fixed64(tl, sF[j]), (unsigned)M);
-        const uint32_t base = lane_off + (uint32_t)op * op_bytes;
-        const uint32_t ro = (uint32_t)(jl * M) + old[e];
-        const uint32_t rn = (uint32_t)(jl * M) + m;
-        *reinterpret_cast<uint32_t*>(hs + base + (ro >> 3) * 256u + (ro & 7u) * 16u) = 0u;
-        *reinterpret_cast<uint32_t*>(hs + base + (rn >> 3) * 256u + (rn & 7u) * 16u) = kOneOne;
-        old[e] = (uint8_t)m;
-      }
-      fence_async_smem();
-      __syncthreads();
-      if (tid == 0) {
-        if (!mbar_wait(&bar_v[vs], ph_v[vs])) {
-          fail = true;
-        } else {
+      // epilogue: warps 0-7, warp w reads TMEM lanes 32 (w % 4) .. + 31 of accumulator w / 4
+      if (warp < 8) {
+        if (!fail && nch > 0) {
+          fail = !mbar_wait_ab(bar_acc, ph_acc, s_abort);
           fence_after_sync();
-          const uint32_t va = smem_addr(sV + vs * kShChunkBytes), ha = smem_addr(hs);
-#pragma unroll
-          for (int ks = 0; ks < kShKSteps; ++ks) {
-            const uint64_t dv = smem_desc(va + (uint32_t)ks * (kShRows * 32u));
-            const uint32_t acc = (ch > 0 || ks > 0) ? 1u : 0u;
-#pragma unroll
-            for (int op = 0; op < 2; ++op)
-              mma_f16(tmem + (uint32_t)op * 256u, dv,
-                      smem_desc(ha + (uint32_t)op * op_bytes + (uint32_t)ks * (uint32_t)(Nm * 32)), idesc, acc);
-          }
-          mma_commit(&bar_mma[s]);
         }
-      }
-      ph_v[vs] ^= 1u;
-      pend[s] = true;
-    }
-    // drain this item's MMAs
-    for (int s = 0; s < 2; ++s)
-      if (pend[s]) {
-        fail |= !mbar_wait(&bar_mma[s], ph_mma[s]);
-        ph_mma[s] ^= 1u;
-        pend[s] = false;
-      }
-    if (__syncthreads_or(fail)) abort = true;
-    if (abort) break;
-    fence_after_sync();
-    // the next item's first two V chunks load during this epilogue
-    const int64_t next = item + gridDim.x;
-    if (tid == 0 && next < items) {
-      const unsigned char* img2 = a.image + (size_t)(next / a.npass) * (size_t)nch * kShChunkBytes;
-      for (int64_t c = 0; c < 2 && c < nch; ++c)
-        bulk_load(sV + c * kShChunkBytes, img2 + (size_t)c * kShChunkBytes, kShChunkBytes, &bar_v[c]);
-    }
-
-    // epilogue (warps 0-7): warp w reads TMEM lanes 32 (w % 4) .. + 31 of accumulator w / 4
-    if (warp < 8) {
-      const int quarter = warp & 3, op = warp >> 2;
-      const int row = quarter * 32 + lane;
-      const int64_t c = g * kShCurves + (row >> 1);
-      const bool even = (row & 1) == 0;
-      const bool cvalid = c < a.ncurves;
-      const float sa = cvalid ? a.inv_scale[2 * c] : 0.f, sw = cvalid ? a.inv_scale[2 * c + 1] : 0.f;
-      const bool cbad = cvalid && a.curve_bad[c];
-      float acc = 0.f;
-      int m = 0, jl = 0;
-      const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)op * 256u;
-      for (int c0 = 0; c0 < rows_used; c0 += 32) {
-        uint32_t v[32];
-        if (nch > 0) {
-          tmem_ld32(tbase + (uint32_t)c0, v);
-        } else {
+        fail = __any_sync(0xffffffffu, fail);
+        if (fail && lane == 0) *s_abort = 1;
+        if (!fail) {
+          // lanes 2c and 2c + 1 hold the A and B rows of curve c; the even lane
+          // reduces, the odd lane supplies B by shuffle. Loads of 32 columns
+          // at multiples of 32 stay inside the accumulator's 256 columns.
+          const int quarter = warp & 3, op = warp >> 2;
+          const int row = quarter * 32 + lane;
+          const int64_t c = g * kShCurves + (row >> 1);
+          const bool even = (row & 1) == 0;
+          const bool cvalid = c < a.ncurves;
+          const float sa = cvalid ? a.inv_scale[2 * c] : 0.f, sw = cvalid ? a.inv_scale[2 * c + 1] : 0.f;
+          const bool cbad = cvalid && a.curve_bad[c];
+          float acc = 0.f;
+          int m = 0, jl = 0;
+          const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)op * 256u;
+          for (int c0 = 0; c0 < rows_used; c0 += 32) {
+            uint32_t v[32];
+            if (nch > 0) {
+              tmem_ld32(tbase + (uint32_t)c0, v);
+            } else {
 #pragma unroll
-          for (int u = 0; u < 32; ++u) v[u] = 0u;
-        }
-#pragma unroll
-        for (int u = 0; u < 32; ++u) {
-          if (c0 + u < rows_used) {
-            const float val = __uint_as_float(v[u]);
-            const float other = __shfl_xor_sync(0xffffffffu, val, 1);
-            if (even) {
-              const float A = val * sa, B = other * sw;
-              const float den = B + cal;
-              acc += den > 0.f ? (A * A) / den : 0.f;
+              for (int u = 0; u < 32; ++u) v[u] = 0u;
             }
-            if (++m == M) {
-              const int64_t fi = f0 + (int64_t)op * fpm + jl;
-              if (even && cvalid && fi < F) {
-                const float S = cbad ? __int_as_float(0x7fc00000) : acc;
-                if (a.S32) a.S32[c * F + fi] = S;
-                if (a.S_out) a.S_out[c * F + fi] = (double)S;
+            // the 32 column terms first (independent, branch-free), then the
+            // per-frequency sums and stores
+            float tv[32];
+#pragma unroll
+            for (int u = 0; u < 32; ++u) {
+              const float val = __uint_as_float(v[u]);
+              const float other = __shfl_xor_sync(0xffffffffu, val, 1);
+              const float A = val * sa;
+              const float den = other * sw + cal;
+              tv[u] = den > 0.f ? (A * A) * __frcp_rn(den) : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < 32; ++u) {
+              if (c0 + u < rows_used) {
+                acc += tv[u];
+                if (++m == M) {
+                  const int64_t fi = f0 + (int64_t)op * fpm + jl;
+                  if (even && cvalid && fi < F) {
+                    const float S = cbad ? __int_as_float(0x7fc00000) : acc;
+                    if (a.S32) a.S32[c * F + fi] = S;
+                    if (a.S_out) a.S_out[c * F + fi] = (double)S;
+                  }
+                  acc = 0.f;
+                  m = 0;
+                  ++jl;
+                }
               }
-              acc = 0.f;
-              m = 0;
-              ++jl;
             }
           }
+          fence_before_sync();
+          __syncwarp();
+          if (nch > 0 && lane == 0) mbar_arrive(bar_tfree);
         }
       }
+      ph_acc ^= 1u;
     }
-    fence_before_sync();
-    __syncthreads();
-  }
-  // teardown: nothing of this CTA may still be in flight when TMEM is freed
-  // (MMAs; and V loads issued for an item that was not started)
-  for (int s = 0; s < 2; ++s)
-    if (pend[s]) {
-      if (!mbar_wait(&bar_mma[s], ph_mma[s])) fail = true;
-      pend[s] = false;
+    if (fail) {
+      *s_abort = 1;
+      atomicOr(a.status, kStatusTimeout);
     }
-  if (abort || fail) {
-    if (fail) atomicOr(a.status, kStatusTimeout);
   }
+  // teardown: on success the last epilogue waited for `acc`, which covers
+  // every MMA, and every V load was waited for; after a failure the issuer
+  // drained its own work above
   fence_before_sync();
   __syncthreads();
   if (warp == 0)
