@@ -76,6 +76,14 @@ __host__ __device__ __forceinline__ uint32_t km_off(uint32_t r, uint32_t q, uint
   return (q >> 4) * (R * 32u) + (r >> 3) * 256u + ((q >> 3) & 1u) * 128u + (r & 7u) * 16u + (q & 7u) * 2u;
 }
 
+// Approximate reciprocal (one special-function instruction, relative error
+// about 2^-23; subnormal results kept).
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 // tcgen05 shared-memory matrix descriptor: unswizzled, K-direction core-matrix
@@ -167,15 +175,10 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
-        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
-        "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
-        "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-      : "r"(taddr));
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+               : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
@@ -518,8 +521,8 @@ __global__ void __launch_bounds__(kShThreads, 1) shared_mma_kernel(const SharedA
         if (fail && lane == 0) *s_abort = 1;
         if (!fail) {
           // lanes 2c and 2c + 1 hold the A and B rows of curve c; the even lane
-          // reduces, the odd lane supplies B by shuffle. Loads of 32 columns
-          // at multiples of 32 stay inside the accumulator's 256 columns.
+          // reduces, the odd lane supplies B by shuffle. Loads of 8 columns
+          // at multiples of 8 stay inside the accumulator's 256 columns.
           const int quarter = warp & 3, op = warp >> 2;
           const int row = quarter * 32 + lane;
           const int64_t c = g * kShCurves + (row >> 1);
@@ -530,41 +533,43 @@ __global__ void __launch_bounds__(kShThreads, 1) shared_mma_kernel(const SharedA
           float acc = 0.f;
           int m = 0, jl = 0;
           const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)op * 256u;
-          for (int c0 = 0; c0 < rows_used; c0 += 32) {
-            uint32_t v[32];
+          // this curve's outputs for the accumulator's first frequency; only
+          // the even lane stores, only for frequencies below F
+          const int64_t fbase = f0 + (int64_t)op * fpm;
+          const int jmax = (int)((F - fbase) < fpm ? (F - fbase) : fpm);
+          const bool store = even && cvalid;
+          float* const s32 = store && a.S32 ? a.S32 + c * F + fbase : nullptr;
+          double* const s64 = store && a.S_out ? a.S_out + c * F + fbase : nullptr;
+          const float nan = __int_as_float(0x7fc00000);
+          // 8 columns per step in a compact loop
+          for (int c0 = 0; c0 < rows_used; c0 += 8) {
+            uint32_t v[8];
             if (nch > 0) {
-              tmem_ld32(tbase + (uint32_t)c0, v);
+              tmem_ld8(tbase + (uint32_t)c0, v);
             } else {
 #pragma unroll
-              for (int u = 0; u < 32; ++u) v[u] = 0u;
+              for (int u = 0; u < 8; ++u) v[u] = 0u;
             }
-            // the 32 column terms first (independent, branch-free), then the
-            // per-frequency sums and stores
-            float tv[32];
+            float tv[8];
 #pragma unroll
-            for (int u = 0; u < 32; ++u) {
+            for (int u = 0; u < 8; ++u) {  // independent, branch-free column terms
               const float val = __uint_as_float(v[u]);
               const float other = __shfl_xor_sync(0xffffffffu, val, 1);
               const float A = val * sa;
               const float den = other * sw + cal;
-              tv[u] = den > 0.f ? (A * A) * __frcp_rn(den) : 0.f;
+              tv[u] = (den >= 1.17549435e-38f && c0 + u < rows_used) ? (A * A) * rcp_approx(den) : 0.f;
             }
 #pragma unroll
-            for (int u = 0; u < 32; ++u) {
-              if (c0 + u < rows_used) {
-                acc += tv[u];
-                if (++m == M) {
-                  const int64_t fi = f0 + (int64_t)op * fpm + jl;
-                  if (even && cvalid && fi < F) {
-                    const float S = cbad ? __int_as_float(0x7fc00000) : acc;
-                    if (a.S32) a.S32[c * F + fi] = S;
-                    if (a.S_out) a.S_out[c * F + fi] = (double)S;
-                  }
-                  acc = 0.f;
-                  m = 0;
-                  ++jl;
-                }
+            for (int u = 0; u < 8; ++u) {
+              acc += tv[u];
+              const bool endf = c0 + u < rows_used && m + 1 == M;
+              if (endf && jl < jmax) {
+                if (s32) s32[jl] = cbad ? nan : acc;
+                if (s64) s64[jl] = cbad ? (double)nan : (double)acc;
               }
+              acc = endf ? 0.f : acc;
+              m = endf ? 0 : m + 1;
+              jl += endf ? 1 : 0;
             }
           }
           fence_before_sync();
