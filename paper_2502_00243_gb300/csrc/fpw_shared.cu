@@ -45,7 +45,7 @@ constexpr int kShObs = 32;                      // observations per chunk
 constexpr int kShK = 2 * kShObs;                // K entries per chunk (hi, lo)
 constexpr int kShKSteps = kShK / 16;            // MMA k-steps per chunk
 constexpr int kShChunkBytes = kShRows * kShK * 2;  // V image of one chunk: 16 KB
-constexpr int kShThreads = 512;
+constexpr int kShThreads = 576;  // 16 builder/epilogue warps + 2 issuer warps
 constexpr int kShNMax = 256;                    // MMA N limit (M = 128)
 constexpr int kShMaxFpm = 64;                   // frequencies per accumulator, at most
 constexpr int kShHOperandMax = kShNMax * kShK * 2;   // one H operand of a chunk: 32 KB
@@ -65,7 +65,8 @@ constexpr int kOffH = kOffV + kShVSlots * kShChunkBytes;   // H chunks: 2 x 64 K
 constexpr int kOffOld = kOffH + 2 * kShHSlotBytes;         // bin of every (frequency, observation) pair in H, per slot
 constexpr int kOffF = kOffOld + 2 * kMaxPairs;             // the pass's frequencies (binary64)
 constexpr int kOffStage = kOffF + kMaxPassFreqs * 8;       // t, P, D of kShStage observations
-constexpr int kOffBar = kOffStage + 3 * kShStage * 8;
+constexpr int kOffPart = kOffStage + 3 * kShStage * 8;    // epilogue: partial S of a frequency split between warps
+constexpr int kOffBar = kOffPart + 2 * 128 * 4;
 constexpr int kSmemBytes = kOffBar + 128;
 
 // Byte offset of element (row r, k-entry q) of a K-major, unswizzled operand
@@ -298,8 +299,9 @@ __global__ void shared_steps_kernel(const SharedArgs a) {
 //    to `empty` (and to `acc` after an item's last chunk).
 // No block-wide barrier inside the loop; every wait is bounded and gives up
 // when another role has set the abort flag.
-constexpr int kShBuilderWarps = kShThreads / 32 - 1;
+constexpr int kShBuilderWarps = 16;
 constexpr int kShBuilders = kShBuilderWarps * 32;
+constexpr int kShIssuers = kShThreads / 32 - kShBuilderWarps;  // one per accumulator
 
 __global__ void __launch_bounds__(kShThreads, 1) shared_mma_kernel(const SharedArgs a) {
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -337,11 +339,11 @@ __global__ void __launch_bounds__(kShThreads, 1) shared_mma_kernel(const SharedA
   if (tid == 0) {
     for (int q = 0; q < 2; ++q) {
       mbar_init_n(&bar_full[q], kShBuilderWarps);
-      mbar_init_n(&bar_empty[q], 1);
+      mbar_init_n(&bar_empty[q], kShIssuers);
     }
     for (int v = 0; v < kShVSlots; ++v) mbar_init_n(&bar_v[v], 1);
-    mbar_init_n(bar_acc, 1);
-    mbar_init_n(bar_tfree, 8);
+    mbar_init_n(bar_acc, kShIssuers);
+    mbar_init_n(bar_tfree, kShBuilderWarps);
     *s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -372,8 +374,10 @@ __global__ void __launch_bounds__(kShThreads, 1) shared_mma_kernel(const SharedA
   const uint32_t tmem = *tslot;
   bool fail = false;
 
-  if (warp == kShBuilderWarps) {
-    // ------------------------------------------------------------ issuer
+  if (warp >= kShBuilderWarps) {
+    // ------------------------------------------------------------ issuers: warp 16 drives accumulator 0 and
+    // the V loads, warp 17 accumulator 1; both commit to `empty` and `acc` (count 2)
+    const int iop = warp - kShBuilderWarps;
     if (lane == 0 && my_items > 0 && nch > 0) {
       const uint32_t idesc = mma_idesc(kShRows, Nm);
       // descriptors of chunk operands: a base descriptor plus the byte offset / 16
@@ -393,37 +397,36 @@ __global__ void __launch_bounds__(kShThreads, 1) shared_mma_kernel(const SharedA
           limg = a.image + (size_t)(it / a.npass) * (size_t)nch * kShChunkBytes;
         }
       };
-      for (int64_t c = 0; c < 2 && c < total; ++c) load_next((int)c);
+      if (iop == 0)
+        for (int64_t c = 0; c < 2 && c < total; ++c) load_next((int)c);
       uint32_t ph_full[2] = {0u, 0u}, ph_v[kShVSlots] = {0u, 0u, 0u, 0u}, ph_tfree = 0u;
       uint32_t commits[2] = {0u, 0u};
-      bool v_out[kShVSlots] = {total > 0, total > 1, false, false};  // a load is in flight in the slot
+      bool v_out[kShVSlots] = {iop == 0 && total > 0, iop == 0 && total > 1, false, false};  // own loads in flight
       int64_t ch = 0;
       for (int64_t gc = 0; gc < total && !fail; ++gc, ch = (ch + 1 == nch) ? 0 : ch + 1) {
         const int s = (int)(gc & 1), vs = (int)(gc & (kShVSlots - 1));
         if (!mbar_wait_ab(&bar_full[s], ph_full[s], s_abort)) { fail = true; break; }
         ph_full[s] ^= 1u;
-        if (gc + 2 < total) {  // its slot was last read by the MMAs of gc - 2, done before `full` of gc
+        if (iop == 0 && gc + 2 < total) {  // its slot was last read by the MMAs of gc - 2, done before `full` of gc
           const int v2 = (int)((gc + 2) & (kShVSlots - 1));
           load_next(v2);
           v_out[v2] = true;
         }
         if (!mbar_wait_ab(&bar_v[vs], ph_v[vs], s_abort)) { fail = true; break; }
         ph_v[vs] ^= 1u;
-        v_out[vs] = false;
+        if (iop == 0) v_out[vs] = false;
         if (ch == 0 && gc > 0) {  // the previous item's accumulators have been read
           if (!mbar_wait_ab(bar_tfree, ph_tfree, s_abort)) { fail = true; break; }
           ph_tfree ^= 1u;
         }
         fence_after_sync();
         const uint64_t dvs = dv0 + (uint64_t)((vs * kShChunkBytes) >> 4);
-        const uint64_t dhs = dh0 + (uint64_t)((s * kShHSlotBytes) >> 4);
+        const uint64_t dhs = dh0 + (uint64_t)((s * kShHSlotBytes + iop * (int)op_bytes) >> 4);
 #pragma unroll
         for (int ks = 0; ks < kShKSteps; ++ks) {
           const uint32_t acc = (ch > 0 || ks > 0) ? 1u : 0u;
-          const uint64_t dvk = dvs + (uint64_t)((ks * kShRows * 32) >> 4);
-          const uint64_t dhk = dhs + (uint64_t)(((uint32_t)ks * (uint32_t)(Nm * 32)) >> 4);
-          mma_f16(tmem, dvk, dhk, idesc, acc);
-          mma_f16(tmem + 256u, dvk, dhk + (uint64_t)(op_bytes >> 4), idesc, acc);
+          mma_f16(tmem + (uint32_t)iop * 256u, dvs + (uint64_t)((ks * kShRows * 32) >> 4),
+                  dhs + (uint64_t)(((uint32_t)ks * (uint32_t)(Nm * 32)) >> 4), idesc, acc);
         }
         mma_commit(&bar_empty[s]);
         ++commits[s];
@@ -511,72 +514,85 @@ __global__ void __launch_bounds__(kShThreads, 1) shared_mma_kernel(const SharedA
           if (lane == 0) mbar_arrive(&bar_full[s]);
         }
       }
-      // epilogue: warps 0-7, warp w reads TMEM lanes 32 (w % 4) .. + 31 of accumulator w / 4
-      if (warp < 8) {
-        if (!fail && nch > 0) {
-          fail = !mbar_wait_ab(bar_acc, ph_acc, s_abort);
-          fence_after_sync();
-        }
-        fail = __any_sync(0xffffffffu, fail);
-        if (fail && lane == 0) *s_abort = 1;
-        if (!fail) {
-          // lanes 2c and 2c + 1 hold the A and B rows of curve c; the even lane
-          // reduces, the odd lane supplies B by shuffle. Loads of 8 columns
-          // at multiples of 8 stay inside the accumulator's 256 columns.
-          const int quarter = warp & 3, op = warp >> 2;
-          const int row = quarter * 32 + lane;
-          const int64_t c = g * kShCurves + (row >> 1);
-          const bool even = (row & 1) == 0;
-          const bool cvalid = c < a.ncurves;
-          const float sa = cvalid ? a.inv_scale[2 * c] : 0.f, sw = cvalid ? a.inv_scale[2 * c + 1] : 0.f;
-          const bool cbad = cvalid && a.curve_bad[c];
-          float acc = 0.f;
-          int m = 0, jl = 0;
-          const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)op * 256u;
-          // this curve's outputs for the accumulator's first frequency; only
-          // the even lane stores, only for frequencies below F
-          const int64_t fbase = f0 + (int64_t)op * fpm;
-          const int jmax = (int)((F - fbase) < fpm ? (F - fbase) : fpm);
-          const bool store = even && cvalid;
-          float* const s32 = store && a.S32 ? a.S32 + c * F + fbase : nullptr;
-          double* const s64 = store && a.S_out ? a.S_out + c * F + fbase : nullptr;
-          const float nan = __int_as_float(0x7fc00000);
-          // 8 columns per step in a compact loop
-          for (int c0 = 0; c0 < rows_used; c0 += 8) {
-            uint32_t v[8];
-            if (nch > 0) {
-              tmem_ld8(tbase + (uint32_t)c0, v);
-            } else {
+      // epilogue: all builder warps. Warp w reads TMEM lanes 32 (w % 4) .. + 31
+      // of accumulator (w / 4) % 2, columns [0, split) for w < 8 and
+      // [split, fpm M) above (split a multiple of 8 near the middle); the
+      // partial sum of a frequency that straddles the split is handed over
+      // through shared memory.
+      float* sPart = reinterpret_cast<float*>(smem + kOffPart);
+      if (!fail && nch > 0) {
+        fail = !mbar_wait_ab(bar_acc, ph_acc, s_abort);
+        fence_after_sync();
+      }
+      fail = __any_sync(0xffffffffu, fail);
+      if (fail && lane == 0) *s_abort = 1;
+      const int quarter = warp & 3, op = (warp >> 2) & 1, half = warp >> 3;
+      const int row = quarter * 32 + lane;
+      const int64_t c = g * kShCurves + (row >> 1);
+      const bool even = (row & 1) == 0;
+      const bool cvalid = c < a.ncurves;
+      const int split = ((rows_used + 15) >> 4) << 3;
+      const int js = split / M;                          // frequency holding column `split`
+      const bool straddle = split < rows_used && split % M != 0;
+      const int64_t fbase = f0 + (int64_t)op * fpm;
+      const int jmax = (int)((F - fbase) < fpm ? (F - fbase) : fpm);
+      const bool cbad = cvalid && a.curve_bad[c];
+      const bool store = even && cvalid;
+      float* const s32 = store && a.S32 ? a.S32 + c * F + fbase : nullptr;
+      double* const s64 = store && a.S_out ? a.S_out + c * F + fbase : nullptr;
+      const float nan = __int_as_float(0x7fc00000);
+      float acc = 0.f;
+      if (!fail) {
+        // lanes 2c and 2c + 1 hold the A and B rows of curve c; the even lane
+        // reduces, the odd lane supplies B by shuffle
+        const float sa = cvalid ? a.inv_scale[2 * c] : 0.f, sw = cvalid ? a.inv_scale[2 * c + 1] : 0.f;
+        const int cb = half == 0 ? 0 : split, ce = half == 0 ? split : rows_used;
+        int jl = cb / M, m = cb - jl * M;
+        const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)op * 256u;
+        // 8 columns per step in a compact loop
+        for (int c0 = cb; c0 < ce; c0 += 8) {
+          uint32_t v[8];
+          if (nch > 0) {
+            tmem_ld8(tbase + (uint32_t)c0, v);
+          } else {
 #pragma unroll
-              for (int u = 0; u < 8; ++u) v[u] = 0u;
-            }
-            float tv[8];
+            for (int u = 0; u < 8; ++u) v[u] = 0u;
+          }
+          float tv[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {  // independent, branch-free column terms
-              const float val = __uint_as_float(v[u]);
-              const float other = __shfl_xor_sync(0xffffffffu, val, 1);
-              const float A = val * sa;
-              const float den = other * sw + cal;
-              tv[u] = (den >= 1.17549435e-38f && c0 + u < rows_used) ? (A * A) * rcp_approx(den) : 0.f;
-            }
+          for (int u = 0; u < 8; ++u) {  // independent, branch-free column terms
+            const float val = __uint_as_float(v[u]);
+            const float other = __shfl_xor_sync(0xffffffffu, val, 1);
+            const float A = val * sa;
+            const float den = other * sw + cal;
+            tv[u] = (den >= 1.17549435e-38f && c0 + u < ce) ? (A * A) * rcp_approx(den) : 0.f;
+          }
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-              acc += tv[u];
-              const bool endf = c0 + u < rows_used && m + 1 == M;
-              if (endf && jl < jmax) {
+          for (int u = 0; u < 8; ++u) {
+            acc += tv[u];
+            const bool endf = c0 + u < ce && m + 1 == M;
+            if (endf) {
+              if (half == 1 && straddle && jl == js) {
+                sPart[op * 128 + row] = acc;  // the second part of the straddling frequency
+              } else if (jl < jmax) {
                 if (s32) s32[jl] = cbad ? nan : acc;
                 if (s64) s64[jl] = cbad ? (double)nan : (double)acc;
               }
-              acc = endf ? 0.f : acc;
-              m = endf ? 0 : m + 1;
-              jl += endf ? 1 : 0;
             }
+            acc = endf ? 0.f : acc;
+            m = endf ? 0 : m + 1;
+            jl += endf ? 1 : 0;
           }
-          fence_before_sync();
-          __syncwarp();
-          if (nch > 0 && lane == 0) mbar_arrive(bar_tfree);
         }
       }
+      fence_before_sync();
+      builders_sync(kShBuilders);  // partial sums visible; every TMEM read of this item done
+      if (!fail && half == 0 && straddle && js < jmax) {
+        const float S = acc + sPart[op * 128 + row];
+        if (s32) s32[js] = cbad ? nan : S;
+        if (s64) s64[js] = cbad ? (double)nan : (double)S;
+      }
+      if (!fail && nch > 0 && lane == 0) mbar_arrive(bar_tfree);
       ph_acc ^= 1u;
     }
     if (fail) {
