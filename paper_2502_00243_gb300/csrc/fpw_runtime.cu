@@ -123,7 +123,7 @@ struct fpw_ctx {
   cudaStream_t last_stream = nullptr;
   cudaStream_t own_stream = nullptr;
   DevBuf aw, cand_S, cand_idx, curve_bad, words, dense, tile_dev;
-  DevBuf sh_image, sh_scale, sh_S32, sh_step;  // shared-timestamp path scratch
+  DevBuf sh_image, sh_scale, sh_S32, sh_step, sh_sink;  // shared-timestamp path scratch
   DevBuf h_off, h_t, h_x, h_sigma, h_freqs, h_idx, h_S;  // device copies for the host entry point
   std::vector<int64_t> off_host;                          // host copy of offsets (when not supplied)
   std::vector<Plan*> plans;
@@ -716,7 +716,7 @@ int fpw_ctx_destroy(fpw_ctx* ctx) {
     ctx->plans.clear();
     for (DevBuf* b : {&ctx->aw, &ctx->cand_S, &ctx->cand_idx, &ctx->curve_bad, &ctx->words, &ctx->dense, &ctx->tile_dev, &ctx->h_off,
                       &ctx->h_t, &ctx->h_x, &ctx->h_sigma, &ctx->h_freqs, &ctx->h_idx, &ctx->h_S, &ctx->sh_image,
-                      &ctx->sh_scale, &ctx->sh_S32, &ctx->sh_step})
+                      &ctx->sh_scale, &ctx->sh_S32, &ctx->sh_step, &ctx->sh_sink})
       free_buf(*b);
     if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
     for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
@@ -1085,11 +1085,14 @@ int fpw_periodogram_shared(fpw_ctx* ctx, void* stream, const fpw_params* params,
   FPW_CK(ensure(ctx->sh_image, std::max<size_t>(shared_image_bytes(ncurves, n), 256)));
   FPW_CK(ensure(ctx->sh_scale, (size_t)(a.ngroups * per) * 2 * sizeof(float)));
   FPW_CK(ensure(ctx->sh_step, sizeof(unsigned long long) * (size_t)(n + 1)));
+  FPW_CK(ensure(ctx->sh_sink, 32 * 64 * (sizeof(float) + sizeof(double))));
   FPW_CK(ensure(ctx->curve_bad, (size_t)(a.ngroups * per) + 16));
   if (k > 0) FPW_CK(ensure(ctx->sh_S32, (size_t)ncurves * (size_t)nfreq * sizeof(float)));
   a.image = static_cast<unsigned char*>(ctx->sh_image.p);
   a.inv_scale = static_cast<float*>(ctx->sh_scale.p);
   a.step = static_cast<unsigned long long*>(ctx->sh_step.p);
+  a.scratch64 = static_cast<double*>(ctx->sh_sink.p);
+  a.scratch32 = reinterpret_cast<float*>(a.scratch64 + 32 * 64);
   a.tmax_bits = reinterpret_cast<unsigned long long*>(static_cast<unsigned*>(ctx->words.p) + 8);
   a.curve_bad = static_cast<uint8_t*>(ctx->curve_bad.p);
   a.S32 = k > 0 ? static_cast<float*>(ctx->sh_S32.p) : nullptr;

@@ -53,6 +53,9 @@ constexpr int kShHSlotBytes = 2 * kShHOperandMax;    // two H operands (two accu
 constexpr int kShTmemCols = 512;
 constexpr unsigned kOneOne = 0x3C003C00u;       // two fp16 1.0
 constexpr long long kWaitClocks = 4000000000LL; // ~2 s at 2 GHz
+// A waiting thread is suspended in mbarrier.try_wait until the phase completes
+// or this many nanoseconds pass (so waiting warps do not take issue slots).
+constexpr uint32_t kSuspendNs = 20000u;
 constexpr int kMaxPassFreqs = 2 * kShMaxFpm;
 constexpr int kMaxPairs = kMaxPassFreqs * kShObs;
 constexpr int kShVSlots = 4;                    // V chunks in flight: loads run two chunks ahead
@@ -108,9 +111,9 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   while (true) {
     uint32_t done;
     asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
         : "=r"(done)
-        : "r"(smem_addr(bar)), "r"(parity)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(kSuspendNs)
         : "memory");
     if (done) return true;
     if (clock64() - t0 > kWaitClocks) return false;
@@ -123,9 +126,9 @@ __device__ __forceinline__ bool mbar_wait_ab(uint64_t* bar, uint32_t parity, vol
   while (true) {
     uint32_t done;
     asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
         : "=r"(done)
-        : "r"(smem_addr(bar)), "r"(parity)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(kSuspendNs)
         : "memory");
     if (done) return true;
     if (*abort || clock64() - t0 > kWaitClocks) return false;
@@ -176,11 +179,20 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
+// tcgen05.ld of 8 columns without the wait; the registers are valid only after
+// tmem_wait_ld8 on the same array, which names them as operands so that no
+// use of them can be scheduled before the wait.
+__device__ __forceinline__ void tmem_ld8_issue(uint32_t taddr, uint32_t (&v)[8]) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
                : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_ld8(uint32_t (&v)[8]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7])
+               :
+               : "memory");
 }
 
 __device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -529,7 +541,6 @@ __global__ void __launch_bounds__(kShThreads, 1) shared_mma_kernel(const SharedA
       const int quarter = warp & 3, op = (warp >> 2) & 1, half = warp >> 3;
       const int row = quarter * 32 + lane;
       const int64_t c = g * kShCurves + (row >> 1);
-      const bool even = (row & 1) == 0;
       const bool cvalid = c < a.ncurves;
       const int split = ((rows_used + 15) >> 4) << 3;
       const int js = split / M;                          // frequency holding column `split`
@@ -537,10 +548,13 @@ __global__ void __launch_bounds__(kShThreads, 1) shared_mma_kernel(const SharedA
       const int64_t fbase = f0 + (int64_t)op * fpm;
       const int jmax = (int)((F - fbase) < fpm ? (F - fbase) : fpm);
       const bool cbad = cvalid && a.curve_bad[c];
-      const bool store = even && cvalid;
-      float* const s32 = store && a.S32 ? a.S32 + c * F + fbase : nullptr;
-      double* const s64 = store && a.S_out ? a.S_out + c * F + fbase : nullptr;
+      // both lanes of a pair store the even lane's sum to the same address
+      // (one transaction, no divergent branch before the next shuffle); lanes
+      // of padding curves write into a scratch area instead
+      float* const s32 = a.S32 ? (cvalid ? a.S32 + c * F + fbase : a.scratch32 + lane * kShMaxFpm) : nullptr;
+      double* const s64 = a.S_out ? (cvalid ? a.S_out + c * F + fbase : a.scratch64 + lane * kShMaxFpm) : nullptr;
       const float nan = __int_as_float(0x7fc00000);
+      const int pair_lane = lane & ~1;
       float acc = 0.f;
       if (!fail) {
         // lanes 2c and 2c + 1 hold the A and B rows of curve c; the even lane
@@ -549,11 +563,17 @@ __global__ void __launch_bounds__(kShThreads, 1) shared_mma_kernel(const SharedA
         const int cb = half == 0 ? 0 : split, ce = half == 0 ? split : rows_used;
         int jl = cb / M, m = cb - jl * M;
         const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)op * 256u;
-        // 8 columns per step in a compact loop
+        // 8 columns per step in a compact loop; the next step's TMEM load is
+        // in flight while this step's columns are reduced
+        uint32_t nx[8];
+        if (nch > 0 && cb < ce) tmem_ld8_issue(tbase + (uint32_t)cb, nx);
         for (int c0 = cb; c0 < ce; c0 += 8) {
           uint32_t v[8];
           if (nch > 0) {
-            tmem_ld8(tbase + (uint32_t)c0, v);
+            tmem_wait_ld8(nx);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = nx[u];
+            if (c0 + 8 < ce) tmem_ld8_issue(tbase + (uint32_t)(c0 + 8), nx);
           } else {
 #pragma unroll
             for (int u = 0; u < 8; ++u) v[u] = 0u;
@@ -570,13 +590,14 @@ __global__ void __launch_bounds__(kShThreads, 1) shared_mma_kernel(const SharedA
 #pragma unroll
           for (int u = 0; u < 8; ++u) {
             acc += tv[u];
-            const bool endf = c0 + u < ce && m + 1 == M;
+            const bool endf = c0 + u < ce && m + 1 == M;  // warp-uniform
             if (endf) {
+              const float S = __shfl_sync(0xffffffffu, acc, pair_lane);
               if (half == 1 && straddle && jl == js) {
-                sPart[op * 128 + row] = acc;  // the second part of the straddling frequency
+                sPart[op * 128 + row] = S;  // the second part of the straddling frequency
               } else if (jl < jmax) {
-                if (s32) s32[jl] = cbad ? nan : acc;
-                if (s64) s64[jl] = cbad ? (double)nan : (double)acc;
+                if (s32) s32[jl] = cbad ? nan : S;
+                if (s64) s64[jl] = cbad ? (double)nan : (double)S;
               }
             }
             acc = endf ? 0.f : acc;
@@ -588,7 +609,7 @@ __global__ void __launch_bounds__(kShThreads, 1) shared_mma_kernel(const SharedA
       fence_before_sync();
       builders_sync(kShBuilders);  // partial sums visible; every TMEM read of this item done
       if (!fail && half == 0 && straddle && js < jmax) {
-        const float S = acc + sPart[op * 128 + row];
+        const float S = __shfl_sync(0xffffffffu, acc, pair_lane) + sPart[op * 128 + (row & ~1)];
         if (s32) s32[js] = cbad ? nan : S;
         if (s64) s64[js] = cbad ? (double)nan : (double)S;
       }

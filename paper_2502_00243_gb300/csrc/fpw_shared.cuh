@@ -29,6 +29,8 @@ struct SharedArgs {
   double inv_alpha2;
   float* S32;               // dense [ncurves][nfreq] FP32 (required when k > 0), or NULL
   double* S_out;            // dense [ncurves][nfreq] or NULL
+  float* scratch32;         // [32 * 64] write sink for padding curves
+  double* scratch64;        // [32 * 64]
   int k;
   int peak_raw;
   int32_t* topk_idx;        // [ncurves][k]
