@@ -25,6 +25,10 @@ Functions and the passages they follow:
 * :func:`topk` -- the k highest local maxima of a periodogram (Section 3.5).
 * :func:`bins` -- bin of every (frequency, observation) pair and the exact
   distance from t*f to the nearest bin edge, for bin-mismatch accounting.
+* :func:`fpw_shared` -- Section 4 / Appendix D batch routine: curves sharing
+  their times, bins computed once per frequency.
+* :func:`fpw_drift` (``drift.py``, numpy) -- Appendix A.1-A.2: the statistic with
+  a polynomial baseline drift marginalised, formed densely.
 """
 from __future__ import annotations
 
@@ -225,3 +229,6 @@ def min_edge_parallel(t, freqs, M: int, nthreads: int | None = None) -> np.ndarr
 
 def version() -> int:
     return int(_load().oracle_version())
+
+
+from .drift import chebyshev_basis, fpw_drift, fpw_drift_chi2_difference  # noqa: E402  (uses bins above)

@@ -470,3 +470,73 @@ def test_shared_batch_equals_single_curve_oracle_and_permutes_rows():
     np.testing.assert_array_equal(S_bad[[0, 1, 3, 4]], S[[0, 1, 3, 4]])
     with pytest.raises(oracle.OracleError):
         oracle.fpw_shared(np.array([0.0, np.inf]), np.zeros((1, 2)), np.ones((1, 2)), w.freqs[:3], 4)
+
+
+# ---------------------------------------------------------------- baseline drift marginalised (Appendix A.1-A.2)
+def test_drift_chebyshev_basis_is_cos_k_theta():
+    theta = np.linspace(0.1, 3.0, 9)
+    t = np.cos(theta)  # tau = t after the span map when the span is exactly [-1, 1]
+    t = np.concatenate([[-1.0], t, [1.0]])
+    Bm = oracle.chebyshev_basis(t, 5, 2.0)
+    tau = 2.0 * (t + 1.0) / 2.0 - 1.0
+    for k in range(5):
+        np.testing.assert_allclose(Bm[:, k], 2.0 * np.cos(k * np.arccos(tau)), rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_drift_sherman_morrison_equals_chi2_difference(seed):
+    """The dense A.2 form against the A.1 definition (difference of two quadratic
+    forms with full covariance matrices), for finite alpha."""
+    rng = np.random.default_rng([41, seed])
+    n, M, K = int(rng.integers(4, 25)), int(rng.choice([2, 3, 5])), int(rng.integers(1, 4))
+    t = np.sort(rng.uniform(0.0, 200.0, n))
+    sigma = rng.uniform(0.2, 1.0, n)
+    x = rng.normal(0, 1, n)
+    alpha, beta = float(rng.uniform(0.5, 3.0)), float(rng.uniform(0.3, 5.0))
+    freqs = rng.uniform(0.05, 2.0, 3)
+    S = oracle.fpw_drift(t, x, sigma, freqs, M, K, beta, 1.0 / alpha ** 2)
+    for q, f in enumerate(freqs):
+        assert S[q] == pytest.approx(oracle.fpw_drift_chi2_difference(t, x, sigma, f, M, K, beta, alpha),
+                                     rel=1e-9, abs=1e-12)
+
+
+def test_drift_reduces_to_eq1_without_baseline_and_as_beta_vanishes():
+    w = L.make("single_plain", nfreq=400)
+    t, x, s = w.curve(0)
+    S1 = oracle.fpw(t, x, s, w.freqs, 10)
+    np.testing.assert_allclose(oracle.fpw_drift(t, x, s, w.freqs, 10, 0, 1.0), S1, rtol=1e-10)
+    np.testing.assert_allclose(oracle.fpw_drift(t, x, s, w.freqs, 10, 3, 1e-7), S1, rtol=1e-8)
+    S1a = oracle.fpw(t, x, s, w.freqs, 10, 0.3)
+    np.testing.assert_allclose(oracle.fpw_drift(t, x, s, w.freqs, 10, 2, 1e-7, 0.3), S1a, rtol=1e-8)
+
+
+def test_drift_absorbs_a_polynomial_baseline_as_beta_grows():
+    """With a nearly flat prior on the baseline coefficients, adding a polynomial
+    of degree < K (in the mapped time) to the fluxes leaves S unchanged."""
+    rng = np.random.default_rng(44)
+    n = 60
+    t = np.sort(rng.uniform(0.0, 500.0, n))
+    sigma = rng.uniform(0.1, 0.3, n)
+    x = 0.4 * np.sin(2 * np.pi * t / 0.731) + rng.normal(0, 1, n) * sigma
+    tau = 2.0 * (t - t.min()) / (t.max() - t.min()) - 1.0
+    drift = 3.0 + 2.0 * tau - 1.5 * (2 * tau ** 2 - 1)
+    freqs = np.linspace(0.5, 3.0, 40)
+    for K in (1, 2, 3):
+        d = np.polynomial.chebyshev.chebval(tau, [3.0, 2.0, -1.5][:K])
+        S0 = oracle.fpw_drift(t, x, sigma, freqs, 8, K, 1e5, 1.0)
+        Sd = oracle.fpw_drift(t, x + d, sigma, freqs, 8, K, 1e5, 1.0)
+        np.testing.assert_allclose(Sd, S0, rtol=1e-6)
+    # without the baseline term the same trend changes S a lot
+    assert np.max(np.abs(oracle.fpw(t, x + drift, sigma, freqs, 8, 1.0) - oracle.fpw(t, x, sigma, freqs, 8, 1.0))) > 1.0
+
+
+def test_drift_ignores_observation_order():
+    rng = np.random.default_rng(45)
+    n = 30
+    t = rng.uniform(0.0, 100.0, n)
+    sigma = rng.uniform(0.2, 0.6, n)
+    x = rng.normal(0, 1, n)
+    f = np.linspace(0.1, 1.0, 20)
+    p = rng.permutation(n)
+    np.testing.assert_allclose(oracle.fpw_drift(t[p], x[p], sigma[p], f, 6, 3, 2.0),
+                               oracle.fpw_drift(t, x, sigma, f, 6, 3, 2.0), rtol=1e-10)
