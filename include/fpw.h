@@ -187,6 +187,32 @@ FPW_API int fpw_periodogram_shared(fpw_ctx* ctx, void* stream, const fpw_params*
                                    int64_t ncurves, const double* x, const double* sigma, const double* freqs,
                                    int64_t nfreq, int M, int k, int32_t* topk_idx, float* topk_S, double* S_out);
 
+/* FPW with a polynomial baseline drift marginalised instead of subtracted
+ * (Appendix A.1-A.2: the general form the paper derives before neglecting the
+ * baseline). Data covariance C_B + C_sigma with C_B = B B^T, B[i, k] =
+ * beta T_k(tau_i) for k < K (Chebyshev polynomials of the first kind in the
+ * curve's times mapped to [-1, 1] over its span), and
+ *   S = u^T (I / alpha^2 + E^T W E)^-1 u,  u = E^T W x,  W = (C_B + C_sigma)^-1,
+ * E the one-hot bin matrix; with 1/alpha^2 = 0 empty bins are dropped. K = 0
+ * (or beta = 0) gives Eq. 1. Bin sums are FP32, the per-frequency K x K solve
+ * binary64.
+ *   offsets, t, x, sigma, freqs, k, topk_idx, topk_S, S_out: as
+ *       fpw_periodogram_batch_ex (device pointers; ncurves <= 65535)
+ *   K: 0..4 basis functions; beta >= 0: prior standard deviation of each
+ *       basis coefficient, in flux units
+ *   M: 1 <= M, with (2 + K) * M * 32 * 4 bytes of shared memory at most
+ *       (FPW_ENOTSUP beyond)
+ * params: FPW_PHASE_FIXED64 and FPW_ACCUM_FP32 only; inv_alpha2 and
+ * peak_mode apply. Scratch held by the context: 24 bytes per observation and,
+ * when k > 0, a dense FP32 periodogram of 4 ncurves nfreq bytes. Reads
+ * offsets[ncurves] back to the host (synchronizes `stream` once).
+ * Errors: FPW_EINVAL, FPW_ENOTSUP, FPW_ENOMEM, FPW_ECUDA; invalid data in a
+ * curve gives S = NaN and no peaks for it (status FPW_EDATA). */
+FPW_API int fpw_periodogram_drift(fpw_ctx* ctx, void* stream, const fpw_params* params, const int64_t* offsets,
+                                  int64_t ncurves, const double* t, const double* x, const double* sigma,
+                                  const double* freqs, int64_t nfreq, int M, int K, double beta, int k,
+                                  int32_t* topk_idx, float* topk_S, double* S_out);
+
 /* Phase entropy (Appendix C) of one set of observation times at every trial
  * frequency: H(f) = -sum_m (N_m/N) log(N_m/N), N_m the observations in phase bin
  * m (bins as the periodogram kernels assign them), natural logarithm, FP32.

@@ -30,7 +30,8 @@ EXPORTED = ("fpw_params_default", "fpw_ctx_create", "fpw_ctx_destroy", "fpw_ctx_
             "fpw_periodogram_ex", "fpw_periodogram_batch", "fpw_periodogram_batch_ex", "fpw_periodogram_batch_host",
             "fpw_debug_bins", "fpw_strerror", "fpw_version", "fpw_last_cuda_error", "fpw_ctx_set_timing",
             "fpw_ctx_kernel_time", "fpw_periodogram_batch_noalloc", "fpw_ctx_set_shape", "fpw_ctx_clear_shapes",
-            "fpw_periodogram_batch_multi", "fpw_phase_entropy", "fpw_phase_entropy_peaks", "fpw_periodogram_shared")
+            "fpw_periodogram_batch_multi", "fpw_phase_entropy", "fpw_phase_entropy_peaks", "fpw_periodogram_shared",
+            "fpw_periodogram_drift")
 
 
 class FPWError(RuntimeError):
@@ -89,6 +90,7 @@ def lib():
                 "fpw_ctx_clear_shapes": (ci, [vp]),
                 "fpw_phase_entropy": (ci, [vp, vp, vp, i64, vp, i64, ci, vp]),
                 "fpw_periodogram_shared": (ci, [vp, vp, P, vp, i64, i64, vp, vp, vp, i64, ci, ci, vp, vp, vp]),
+                "fpw_periodogram_drift": (ci, [vp, vp, P, vp, i64, vp, vp, vp, vp, i64, ci, ci, d, ci, vp, vp, vp]),
                 "fpw_phase_entropy_peaks": (ci, [vp, vp, vp, i64, vp, vp, i64, ci, ci, vp, vp, vp]),
                 "fpw_periodogram_batch_multi": (ci, [vp, vp, P, vp, vp, i64, vp, vp, vp, vp, i64, ci, vp, ci, ci, vp, vp,
                                                      vp, vp]),
@@ -303,6 +305,21 @@ def fpw_periodogram_shared(ctx: Context, stream, params, t, x, sigma, freqs, M: 
         _dev(topk_S, torch.float32, "topk_S") if topk_S is not None else None,
         _dev(S_out, torch.float64, "S_out") if S_out is not None else None)
     _check(rc, "fpw_periodogram_shared")
+
+
+def fpw_periodogram_drift(ctx: Context, stream, params, offsets, t, x, sigma, freqs, M: int, K: int, beta: float,
+                          k: int, topk_idx=None, topk_S=None, S_out=None):
+    """Baseline drift marginalised (Appendix A.1-A.2): ragged batch as for the
+    batched call, K Chebyshev basis functions with prior standard deviation beta."""
+    import torch
+    rc = lib().fpw_periodogram_drift(
+        ctx.handle, _stream(stream), _params(params), _dev(offsets, torch.int64, "offsets"), offsets.numel() - 1,
+        _dev(t, torch.float64, "t"), _dev(x, torch.float64, "x"), _dev(sigma, torch.float64, "sigma"),
+        _dev(freqs, torch.float64, "freqs"), freqs.numel(), int(M), int(K), float(beta), int(k),
+        _dev(topk_idx, torch.int32, "topk_idx") if topk_idx is not None else None,
+        _dev(topk_S, torch.float32, "topk_S") if topk_S is not None else None,
+        _dev(S_out, torch.float64, "S_out") if S_out is not None else None)
+    _check(rc, "fpw_periodogram_drift")
 
 
 def fpw_phase_entropy(ctx: Context, stream, t, freqs, M: int, H_out):

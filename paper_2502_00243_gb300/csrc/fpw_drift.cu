@@ -1,0 +1,337 @@
+// FPW with the baseline drift marginalised (Appendix A.1-A.2) for a ragged
+// batch: the covariance of the data is C_B + C_sigma, C_B = B B^T with a
+// Chebyshev basis B[i, k] = beta T_k(tau_i), k < K (tau: the curve's times
+// mapped to [-1, 1]), and the statistic is
+//
+//   S = u^T (I / alpha^2 + E^T W E)^-1 u,   u = E^T W x,   W = (C_B + C_sigma)^-1.
+//
+// With D = diag(w), H0 = I + B^T D B and g = H0^-1 B^T D x (per curve, once),
+// Woodbury twice reduces it to per-bin sums over the observations in bin m,
+//
+//   Y_m = sum w x,   Bw_m = sum w,   Q_mk = sum w B_ik,
+//
+// and a K x K system per frequency:
+//
+//   z_m = Y_m - Q_m . g,  L_m = Bw_m + 1/alpha^2,
+//   S = sum_m z_m^2 / L_m + v^T H^-1 v,  v = sum_m Q_m z_m / L_m,
+//   H = H0 - sum_m Q_m Q_m^T / L_m   (symmetric positive definite, >= I).
+//
+// Bins with no observation and 1/alpha^2 = 0 are dropped (their rows vanish).
+// The sums accumulate in FP32 in thread-private shared-memory bins (one thread
+// per frequency, (2 + K) floats per bin), phases are the exact 64-bit anchors
+// of the tile kernels stepped across a tile of frequencies; the per-frequency
+// reduction and the K x K Cholesky solve run in binary64.
+#include <math.h>
+
+#include "fpw_shared.cuh"
+
+namespace fpw {
+namespace {
+
+constexpr int kDrMaxK = 4;
+constexpr int kDrPay = 2 + kDrMaxK;  // payload floats per observation: w x, w, w B_0..B_{K-1}
+constexpr int kDrChunk = 256;        // observations staged at a time
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Per curve (one block of 256 threads): validation, the time span, the payload
+// of every observation, H0 = I + B^T D B and g = H0^-1 B^T D x.
+__global__ void __launch_bounds__(256) drift_prep_kernel(const DriftArgs a) {
+  __shared__ double red[8][kDrMaxK * kDrMaxK + kDrMaxK + 3];
+  __shared__ double tl[2];
+  const int64_t c = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int K = a.K;
+  const int64_t o0 = a.offsets[c], n = a.offsets[c + 1] - o0;
+  // validation and the time span
+  double tmin = INFINITY, tmax = -INFINITY;
+  int bad = 0;
+  for (int64_t i = tid; i < n; i += blockDim.x) {
+    const double s = a.sigma[o0 + i], x = a.x[o0 + i], t = a.t[o0 + i];
+    if (!(isfinite(s) && isfinite(x) && isfinite(t) && s > 0.0)) bad = 1;
+    if (isfinite(t)) {
+      tmin = fmin(tmin, t);
+      tmax = fmax(tmax, t);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    tmin = fmin(tmin, __shfl_xor_sync(0xffffffffu, tmin, o));
+    tmax = fmax(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
+    bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+  }
+  if (lane == 0) {
+    red[warp][0] = tmin;
+    red[warp][1] = tmax;
+    red[warp][2] = (double)bad;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double a0 = INFINITY, a1 = -INFINITY, b = 0.0;
+    for (int q = 0; q < 8; ++q) {
+      a0 = fmin(a0, red[q][0]);
+      a1 = fmax(a1, red[q][1]);
+      b = fmax(b, red[q][2]);
+    }
+    tl[0] = a0;
+    tl[1] = a1;
+    a.curve_bad[c] = b > 0.0 ? 1 : 0;
+    if (b > 0.0) atomicOr(a.status, kStatusData);
+  }
+  __syncthreads();
+  const bool cbad = a.curve_bad[c] != 0;
+  const double lo = tl[0], span = tl[1] - tl[0];
+  // payload and the curve sums B^T D B (K x K) and B^T D x (K)
+  double acc[kDrMaxK * kDrMaxK + kDrMaxK];
+#pragma unroll
+  for (int q = 0; q < kDrMaxK * kDrMaxK + kDrMaxK; ++q) acc[q] = 0.0;
+  for (int64_t i = tid; i < n; i += blockDim.x) {
+    float* pay = a.payload + (size_t)(o0 + i) * kDrPay;
+    double w = 0.0, x = 0.0;
+    if (!cbad) {
+      const double s = a.sigma[o0 + i];
+      w = 1.0 / (s * s);
+      x = a.x[o0 + i];
+    }
+    const double tau = (span > 0.0) ? 2.0 * (a.t[o0 + i] - lo) / span - 1.0 : 0.0;
+    double Bk[kDrMaxK];
+    double tkm1 = 1.0, tk = tau;
+#pragma unroll
+    for (int k = 0; k < kDrMaxK; ++k) {
+      double T;
+      if (k == 0) {
+        T = 1.0;
+      } else if (k == 1) {
+        T = tau;
+      } else {
+        const double tn = 2.0 * tau * tk - tkm1;
+        tkm1 = tk;
+        tk = tn;
+        T = tn;
+      }
+      Bk[k] = a.beta * T;
+    }
+    pay[0] = (float)(w * x);
+    pay[1] = (float)w;
+#pragma unroll
+    for (int k = 0; k < kDrMaxK; ++k) {
+      pay[2 + k] = k < K ? (float)(w * Bk[k]) : 0.f;
+      if (k < K) {
+#pragma unroll
+        for (int l = 0; l < kDrMaxK; ++l)
+          if (l < K) acc[k * kDrMaxK + l] += w * Bk[k] * Bk[l];
+        acc[kDrMaxK * kDrMaxK + k] += w * Bk[k] * x;
+      }
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < kDrMaxK * kDrMaxK + kDrMaxK; ++q) {
+    const double v = warp_sum(acc[q]);
+    if (lane == 0) red[warp][q] = v;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double H[kDrMaxK][kDrMaxK], r[kDrMaxK];
+    for (int k = 0; k < K; ++k) {
+      r[k] = 0.0;
+      for (int l = 0; l < K; ++l) {
+        double s = 0.0;
+        for (int q = 0; q < 8; ++q) s += red[q][k * kDrMaxK + l];
+        H[k][l] = s + (k == l ? 1.0 : 0.0);
+      }
+      for (int q = 0; q < 8; ++q) r[k] += red[q][kDrMaxK * kDrMaxK + k];
+    }
+    double* h0 = a.H0 + c * kDrMaxK * kDrMaxK;
+    for (int k = 0; k < kDrMaxK * kDrMaxK; ++k) h0[k] = (k / kDrMaxK < K && k % kDrMaxK < K) ? H[k / kDrMaxK][k % kDrMaxK] : 0.0;
+    // g = H0^-1 B^T D x by Cholesky (H0 >= I is positive definite)
+    double Lc[kDrMaxK][kDrMaxK];
+    for (int k = 0; k < K; ++k)
+      for (int l = 0; l <= k; ++l) {
+        double s = H[k][l];
+        for (int q = 0; q < l; ++q) s -= Lc[k][q] * Lc[l][q];
+        Lc[k][l] = (k == l) ? sqrt(s) : s / Lc[l][l];
+      }
+    double y[kDrMaxK];
+    for (int k = 0; k < K; ++k) {
+      double s = r[k];
+      for (int q = 0; q < k; ++q) s -= Lc[k][q] * y[q];
+      y[k] = s / Lc[k][k];
+    }
+    double* g = a.g + c * kDrMaxK;
+    for (int k = K - 1; k >= 0; --k) {
+      double s = y[k];
+      for (int q = k + 1; q < K; ++q) s -= Lc[q][k] * g[q];
+      g[k] = s / Lc[k][k];
+    }
+    for (int k = K; k < kDrMaxK; ++k) g[k] = 0.0;
+  }
+  if (blockIdx.x == 0)
+    for (int64_t q = tid; q < a.nfreq; q += blockDim.x)
+      if (!isfinite(a.freqs[q])) atomicOr(a.status, kStatusGrid);
+}
+
+// One block per (tile of T frequencies, curve); thread = frequency. Bins
+// [(2 + K) * M][T] floats, thread-private (bank = lane).
+__global__ void __launch_bounds__(128) drift_kernel(const DriftArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int T = blockDim.x, tid = threadIdx.x;
+  const int K = a.K, M = a.M, NP = 2 + K;
+  const int64_t c = blockIdx.y, F = a.nfreq;
+  const int64_t f0 = (int64_t)blockIdx.x * T, k = f0 + tid;
+  float* bins = reinterpret_cast<float*>(smem);                       // [NP * M][T]
+  unsigned long long* sPD = reinterpret_cast<unsigned long long*>(bins + (size_t)NP * M * T);  // [chunk][2]
+  float* sPay = reinterpret_cast<float*>(sPD + 2 * kDrChunk);         // [chunk][kDrPay]
+  const bool grid_bad = (*(volatile unsigned*)a.status & kStatusGrid) != 0u;
+  if (grid_bad) return;
+  const bool cbad = a.curve_bad[c] != 0;
+  const int64_t o0 = a.offsets[c], n = a.offsets[c + 1] - o0;
+  const double df = (F > 1) ? (a.freqs[F - 1] - a.freqs[0]) / (double)(F - 1) : 0.0;
+  const double fa = a.freqs[f0];
+  // linear grid over this tile (the tile kernels' bound on the phase error)?
+  double tm = 0.0;
+  for (int64_t i = tid; i < n; i += T) tm = fmax(tm, fabs(a.t[o0 + i]));
+  __shared__ double s_tm[4];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) tm = fmax(tm, __shfl_xor_sync(0xffffffffu, tm, o));
+  if ((tid & 31) == 0) s_tm[tid >> 5] = tm;
+  __syncthreads();
+  tm = 0.0;
+  for (int q = 0; q < (T >> 5); ++q) tm = fmax(tm, s_tm[q]);
+  const double fk = k < F ? a.freqs[k] : fa;
+  const bool nonlin = k < F && fabs(fk - fma((double)tid, df, fa)) * tm > kGridTolCycles;
+  const bool lin = !__syncthreads_or(nonlin);
+  for (int q = 0; q < NP * M; ++q) bins[q * T + tid] = 0.f;
+  for (int64_t oc = 0; oc < n; oc += kDrChunk) {
+    const int cnt = (int)((n - oc) < kDrChunk ? (n - oc) : kDrChunk);
+    __syncthreads();
+    for (int i = tid; i < cnt; i += T) {
+      const double ti = a.t[o0 + oc + i];
+      sPD[2 * i] = lin ? phase_fixed64(ti, fa) : (unsigned long long)__double_as_longlong(ti);
+      sPD[2 * i + 1] = lin ? phase_fixed64(ti, df) : 0ull;
+      const float* pay = a.payload + (size_t)(o0 + oc + i) * kDrPay;
+#pragma unroll
+      for (int q = 0; q < kDrPay; ++q) sPay[i * kDrPay + q] = pay[q];
+    }
+    __syncthreads();
+    if (!cbad) {
+      for (int i = 0; i < cnt; ++i) {
+        const unsigned long long P = sPD[2 * i], D = sPD[2 * i + 1];
+        const unsigned long long phi =
+            lin ? P + (unsigned long long)tid * D : phase_fixed64(__longlong_as_double((long long)P), fk);
+        const int m = (int)bin_of_phase(phi, (unsigned)M);
+        float* b = bins + (size_t)m * T + tid;
+        const float* pay = sPay + i * kDrPay;
+        for (int q = 0; q < NP; ++q) b[(size_t)q * M * T] += pay[q];
+      }
+    }
+  }
+  if (k >= F) return;
+  // binary64 reduction: S = sum z^2 / L + v^T H^-1 v
+  double H[kDrMaxK][kDrMaxK], v[kDrMaxK], g[kDrMaxK];
+  const double* h0 = a.H0 + c * kDrMaxK * kDrMaxK;
+  for (int p = 0; p < K; ++p) {
+    g[p] = a.g[c * kDrMaxK + p];
+    v[p] = 0.0;
+    for (int q = 0; q < K; ++q) H[p][q] = h0[p * kDrMaxK + q];
+  }
+  const double cal = a.inv_alpha2;
+  double S = 0.0;
+  for (int m = 0; m < M; ++m) {
+    const double Y = bins[(size_t)(0 * M + m) * T + tid];
+    const double Bw = bins[(size_t)(1 * M + m) * T + tid];
+    const double L = Bw + cal;
+    if (!(L > 0.0)) continue;  // empty bin with 1/alpha^2 = 0: dropped
+    double Q[kDrMaxK];
+    double z = Y;
+    for (int p = 0; p < K; ++p) {
+      Q[p] = bins[(size_t)((2 + p) * M + m) * T + tid];
+      z -= Q[p] * g[p];
+    }
+    const double zl = z / L;
+    S += z * zl;
+    for (int p = 0; p < K; ++p) {
+      v[p] += Q[p] * zl;
+      for (int q = 0; q < K; ++q) H[p][q] -= Q[p] * Q[q] / L;
+    }
+  }
+  // v^T H^-1 v by Cholesky (H >= I)
+  double Lc[kDrMaxK][kDrMaxK], y[kDrMaxK];
+  for (int p = 0; p < K; ++p)
+    for (int q = 0; q <= p; ++q) {
+      double s = H[p][q];
+      for (int r = 0; r < q; ++r) s -= Lc[p][r] * Lc[q][r];
+      Lc[p][q] = (p == q) ? sqrt(s > 0.0 ? s : 0.0) : s / Lc[q][q];
+    }
+  for (int p = 0; p < K; ++p) {
+    double s = v[p];
+    for (int r = 0; r < p; ++r) s -= Lc[p][r] * y[r];
+    y[p] = Lc[p][p] > 0.0 ? s / Lc[p][p] : 0.0;
+    S += y[p] * y[p];
+  }
+  const float Sf = cbad ? __int_as_float(0x7fc00000) : (float)S;
+  if (a.S32) a.S32[c * F + k] = Sf;
+  if (a.S_out) a.S_out[c * F + k] = cbad ? (double)Sf : S;
+}
+
+}  // namespace
+
+// Dynamic shared memory the drift kernel may use: the opt-in limit minus its
+// static shared memory.
+static size_t drift_dynamic_limit(int smem_optin) {
+  cudaFuncAttributes fa{};
+  if (cudaFuncGetAttributes(&fa, drift_kernel) != cudaSuccess) return 0;
+  return smem_optin > (int)fa.sharedSizeBytes ? (size_t)(smem_optin - (int)fa.sharedSizeBytes) : 0;
+}
+
+int drift_threads(int M, int K, int smem_optin) {
+  const size_t lim = drift_dynamic_limit(smem_optin);
+  for (int T = 128; T >= 32; T >>= 1)
+    if (drift_smem_bytes(M, K, T) <= lim) return T;
+  return 0;
+}
+
+size_t drift_smem_bytes(int M, int K, int T) {
+  return (size_t)(2 + K) * M * T * 4 + (size_t)kDrChunk * 16 + (size_t)kDrChunk * kDrPay * 4;
+}
+
+int drift_max_basis() { return kDrMaxK; }
+
+int drift_payload_floats() { return kDrPay; }
+
+cudaError_t drift_init_attributes(int max_smem) {
+  return cudaFuncSetAttribute(drift_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)drift_dynamic_limit(max_smem));
+}
+
+cudaError_t launch_drift(const DriftArgs& a, int T, cudaStream_t st) {
+  if (a.ncurves <= 0) return cudaSuccess;
+  drift_prep_kernel<<<(unsigned)a.ncurves, 256, 0, st>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || a.nfreq <= 0) return e;
+  const int64_t tiles = (a.nfreq + T - 1) / T;
+  if (a.timing_start) cudaEventRecord(a.timing_start, st);
+  drift_kernel<<<dim3((unsigned)tiles, (unsigned)a.ncurves), T, drift_smem_bytes(a.M, a.K, T), st>>>(a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (a.timing_stop) cudaEventRecord(a.timing_stop, st);
+  if (a.k > 0) {
+    DenseTopk32Args t{};
+    t.S32 = a.S32;
+    t.nfreq = a.nfreq;
+    t.k = a.k;
+    t.peak_raw = a.peak_raw;
+    t.curve_bad = a.curve_bad;
+    t.status = a.status;
+    t.topk_idx = a.topk_idx;
+    t.topk_S = a.topk_S;
+    e = launch_dense_topk32(t, a.ncurves, st);
+  }
+  return e;
+}
+
+}  // namespace fpw

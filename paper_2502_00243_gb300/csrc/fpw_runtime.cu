@@ -124,6 +124,7 @@ struct fpw_ctx {
   cudaStream_t own_stream = nullptr;
   DevBuf aw, cand_S, cand_idx, curve_bad, words, dense, tile_dev;
   DevBuf sh_image, sh_scale, sh_S32, sh_step, sh_sink;  // shared-timestamp path scratch
+  DevBuf dr_payload, dr_H0, dr_g;                       // baseline-drift path scratch
   DevBuf h_off, h_t, h_x, h_sigma, h_freqs, h_idx, h_S;  // device copies for the host entry point
   std::vector<int64_t> off_host;                          // host copy of offsets (when not supplied)
   std::vector<Plan*> plans;
@@ -688,6 +689,7 @@ int fpw_ctx_create(fpw_ctx** out, int device) {
   }
   if (e == cudaSuccess) e = plain_init_attributes(ctx->smem_optin);
   if (e == cudaSuccess && (size_t)ctx->smem_optin >= shared_smem_bytes()) e = shared_init_attributes();
+  if (e == cudaSuccess) e = drift_init_attributes(ctx->smem_optin);
   if (e == cudaSuccess) e = ensure(ctx->words, 64);
   if (e == cudaSuccess) e = cudaMemset(ctx->words.p, 0, 64);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking);
@@ -716,7 +718,8 @@ int fpw_ctx_destroy(fpw_ctx* ctx) {
     ctx->plans.clear();
     for (DevBuf* b : {&ctx->aw, &ctx->cand_S, &ctx->cand_idx, &ctx->curve_bad, &ctx->words, &ctx->dense, &ctx->tile_dev, &ctx->h_off,
                       &ctx->h_t, &ctx->h_x, &ctx->h_sigma, &ctx->h_freqs, &ctx->h_idx, &ctx->h_S, &ctx->sh_image,
-                      &ctx->sh_scale, &ctx->sh_S32, &ctx->sh_step, &ctx->sh_sink})
+                      &ctx->sh_scale, &ctx->sh_S32, &ctx->sh_step, &ctx->sh_sink, &ctx->dr_payload,
+                      &ctx->dr_H0, &ctx->dr_g})
       free_buf(*b);
     if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
     for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
@@ -1109,6 +1112,83 @@ int fpw_periodogram_shared(fpw_ctx* ctx, void* stream, const fpw_params* params,
   }
   FPW_CK(cudaMemsetAsync(words, 0, 2 * sizeof(unsigned), st));
   FPW_CK(launch_shared(a, ctx->nsm, st));
+  FPW_CK(launch_latch(words, st));
+  return FPW_OK;
+}
+
+int fpw_periodogram_drift(fpw_ctx* ctx, void* stream, const fpw_params* params, const int64_t* offsets,
+                          int64_t ncurves, const double* t, const double* x, const double* sigma, const double* freqs,
+                          int64_t nfreq, int M, int K, double beta, int k, int32_t* topk_idx, float* topk_S,
+                          double* S_out) {
+  if (!ctx || ncurves < 0 || nfreq < 0 || M < 1 || k < 0 || k > FPW_MAX_TOPK) return FPW_EINVAL;
+  if (K < 0 || K > drift_max_basis() || !(beta >= 0.0) || !std::isfinite(beta)) return FPW_EINVAL;
+  if (ncurves > 0 && (!offsets || (nfreq > 0 && !freqs))) return FPW_EINVAL;
+  if (ncurves > 0 && k > 0 && (!topk_idx || !topk_S)) return FPW_EINVAL;
+  if (nfreq > ((int64_t)1 << 31) - 1024 || ncurves > 65535) return FPW_EINVAL;
+  fpw_params p;
+  fpw_params_default(&p);
+  if (params) p = *params;
+  if (!valid_params(p)) return FPW_EINVAL;
+  if (p.phase_mode != FPW_PHASE_FIXED64 || p.accum != FPW_ACCUM_FP32) return FPW_ENOTSUP;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return FPW_ECUDA;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  clear_stale_error();
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  ctx->last_stream = st;
+  const int T = drift_threads(M, K, ctx->smem_optin);
+  if (T == 0) return FPW_ENOTSUP;
+  if (ncurves == 0) return FPW_OK;
+  int64_t nobs = 0;
+  FPW_CK(cudaMemcpyAsync(&nobs, offsets + ncurves, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  FPW_CK(cudaStreamSynchronize(st));
+  if (nobs < 0) return FPW_EINVAL;
+  if (nobs > 0 && (!t || !x || !sigma)) return FPW_EINVAL;
+  unsigned* words = static_cast<unsigned*>(ctx->words.p);
+  if (nfreq == 0) {
+    if (k > 0) FPW_CK(launch_fill_topk(topk_idx, topk_S, ncurves * k, st));
+    return FPW_OK;
+  }
+  FPW_CK(ensure(ctx->dr_payload, sizeof(float) * (size_t)drift_payload_floats() * (size_t)std::max<int64_t>(nobs, 1)));
+  FPW_CK(ensure(ctx->dr_H0, sizeof(double) * 16 * (size_t)ncurves));
+  FPW_CK(ensure(ctx->dr_g, sizeof(double) * 4 * (size_t)ncurves));
+  FPW_CK(ensure(ctx->curve_bad, (size_t)ncurves + 16));
+  if (k > 0) FPW_CK(ensure(ctx->sh_S32, (size_t)ncurves * (size_t)nfreq * sizeof(float)));
+  DriftArgs a{};
+  a.offsets = offsets;
+  a.ncurves = ncurves;
+  a.t = t;
+  a.x = x;
+  a.sigma = sigma;
+  a.freqs = freqs;
+  a.nfreq = nfreq;
+  a.M = M;
+  a.K = K;
+  a.beta = beta;
+  a.inv_alpha2 = p.inv_alpha2;
+  a.payload = static_cast<float*>(ctx->dr_payload.p);
+  a.H0 = static_cast<double*>(ctx->dr_H0.p);
+  a.g = static_cast<double*>(ctx->dr_g.p);
+  a.curve_bad = static_cast<uint8_t*>(ctx->curve_bad.p);
+  a.status = words + 1;
+  a.S32 = k > 0 ? static_cast<float*>(ctx->sh_S32.p) : nullptr;
+  a.S_out = S_out;
+  a.k = k;
+  a.peak_raw = p.peak_mode == FPW_PEAK_RAW ? 1 : 0;
+  a.topk_idx = topk_idx;
+  a.topk_S = topk_S;
+  if (ctx->timing) {
+    while (ctx->ev.size() < ctx->ev_used + 2) {
+      cudaEvent_t e;
+      FPW_CK(cudaEventCreate(&e));
+      ctx->ev.push_back(e);
+    }
+    a.timing_start = ctx->ev[ctx->ev_used];
+    a.timing_stop = ctx->ev[ctx->ev_used + 1];
+    ctx->ev_used += 2;
+  }
+  FPW_CK(cudaMemsetAsync(words, 0, 2 * sizeof(unsigned), st));
+  FPW_CK(launch_drift(a, T, st));
   FPW_CK(launch_latch(words, st));
   return FPW_OK;
 }

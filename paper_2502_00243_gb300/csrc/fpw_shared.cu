@@ -411,22 +411,24 @@ __global__ void __launch_bounds__(kShThreads, 1) shared_mma_kernel(const SharedA
       };
       if (iop == 0)
         for (int64_t c = 0; c < 2 && c < total; ++c) load_next((int)c);
-      uint32_t ph_full[2] = {0u, 0u}, ph_v[kShVSlots] = {0u, 0u, 0u, 0u}, ph_tfree = 0u;
-      uint32_t commits[2] = {0u, 0u};
-      bool v_out[kShVSlots] = {iop == 0 && total > 0, iop == 0 && total > 1, false, false};  // own loads in flight
+      // per-slot phase parities and flags as bit masks in registers (a
+      // run-time-indexed array would live in local memory)
+      uint32_t ph_full = 0u, ph_v = 0u, ph_tfree = 0u;
+      uint32_t commits0 = 0u, commits1 = 0u;
+      uint32_t v_out = iop == 0 ? ((total > 0 ? 1u : 0u) | (total > 1 ? 2u : 0u)) : 0u;  // own loads in flight
       int64_t ch = 0;
       for (int64_t gc = 0; gc < total && !fail; ++gc, ch = (ch + 1 == nch) ? 0 : ch + 1) {
         const int s = (int)(gc & 1), vs = (int)(gc & (kShVSlots - 1));
-        if (!mbar_wait_ab(&bar_full[s], ph_full[s], s_abort)) { fail = true; break; }
-        ph_full[s] ^= 1u;
+        if (!mbar_wait_ab(&bar_full[s], (ph_full >> s) & 1u, s_abort)) { fail = true; break; }
+        ph_full ^= 1u << s;
         if (iop == 0 && gc + 2 < total) {  // its slot was last read by the MMAs of gc - 2, done before `full` of gc
           const int v2 = (int)((gc + 2) & (kShVSlots - 1));
           load_next(v2);
-          v_out[v2] = true;
+          v_out |= 1u << v2;
         }
-        if (!mbar_wait_ab(&bar_v[vs], ph_v[vs], s_abort)) { fail = true; break; }
-        ph_v[vs] ^= 1u;
-        if (iop == 0) v_out[vs] = false;
+        if (!mbar_wait_ab(&bar_v[vs], (ph_v >> vs) & 1u, s_abort)) { fail = true; break; }
+        ph_v ^= 1u << vs;
+        v_out &= ~(1u << vs);
         if (ch == 0 && gc > 0) {  // the previous item's accumulators have been read
           if (!mbar_wait_ab(bar_tfree, ph_tfree, s_abort)) { fail = true; break; }
           ph_tfree ^= 1u;
@@ -441,7 +443,7 @@ __global__ void __launch_bounds__(kShThreads, 1) shared_mma_kernel(const SharedA
                   dhs + (uint64_t)(((uint32_t)ks * (uint32_t)(Nm * 32)) >> 4), idesc, acc);
         }
         mma_commit(&bar_empty[s]);
-        ++commits[s];
+        if (s == 0) ++commits0; else ++commits1;
         if (ch == nch - 1) mma_commit(bar_acc);
       }
       if (fail) {
@@ -450,9 +452,9 @@ __global__ void __launch_bounds__(kShThreads, 1) shared_mma_kernel(const SharedA
         // nothing may be in flight when the CTA frees TMEM and exits: bounded
         // waits for the last commit of each slot and for outstanding V loads
         for (int q = 0; q < 2; ++q)
-          if (commits[q] > 0u) mbar_wait(&bar_empty[q], (commits[q] - 1u) & 1u);
+          if ((q == 0 ? commits0 : commits1) > 0u) mbar_wait(&bar_empty[q], ((q == 0 ? commits0 : commits1) - 1u) & 1u);
         for (int v = 0; v < kShVSlots; ++v)
-          if (v_out[v]) mbar_wait(&bar_v[v], ph_v[v]);
+          if ((v_out >> v) & 1u) mbar_wait(&bar_v[v], (ph_v >> v) & 1u);
       }
     }
   } else {
@@ -461,7 +463,7 @@ __global__ void __launch_bounds__(kShThreads, 1) shared_mma_kernel(const SharedA
     // barrier even after a failure (it then skips the work), so no builder
     // can wait at a barrier for one that left; failure decisions are made
     // warp-uniform before any warp-collective instruction.
-    uint32_t ph_empty[2] = {0u, 0u}, ph_acc = 0u;
+    uint32_t ph_empty = 0u, ph_acc = 0u;  // per-slot parities as bits
     bool staged = false;
     int64_t gc = 0;
     for (int64_t k = 0; k < my_items; ++k) {
@@ -495,8 +497,8 @@ __global__ void __launch_bounds__(kShThreads, 1) shared_mma_kernel(const SharedA
           builders_sync(kShBuilders);
         }
         if (!fail && gc >= 2) {  // the MMAs of gc - 2 read H slot s
-          fail = !mbar_wait_ab(&bar_empty[s], ph_empty[s], s_abort);
-          ph_empty[s] ^= 1u;
+          fail = !mbar_wait_ab(&bar_empty[s], (ph_empty >> s) & 1u, s_abort);
+          ph_empty ^= 1u << s;
         }
         fail = __any_sync(0xffffffffu, fail);
         if (fail && lane == 0) *s_abort = 1;  // the other roles stop waiting
@@ -635,7 +637,7 @@ __global__ void __launch_bounds__(kShThreads, 1) shared_mma_kernel(const SharedA
 // arg-max among peaks ranked strictly after the previous pick.
 constexpr int kShTopkThreads = 512;
 
-__global__ void __launch_bounds__(kShTopkThreads) shared_topk_kernel(const SharedArgs a) {
+__global__ void __launch_bounds__(kShTopkThreads) dense_topk32_kernel(const DenseTopk32Args a) {
   __shared__ float ws[32];
   __shared__ int wi[32];
   const int64_t c = blockIdx.x;
@@ -733,6 +735,12 @@ int shared_freqs_per_mma(int M, int* n_mma) {
   return fpm;
 }
 
+cudaError_t launch_dense_topk32(const DenseTopk32Args& t, int64_t ncurves, cudaStream_t st) {
+  if (t.k <= 0 || ncurves <= 0) return cudaSuccess;
+  dense_topk32_kernel<<<(unsigned)ncurves, kShTopkThreads, 0, st>>>(t);
+  return cudaGetLastError();
+}
+
 cudaError_t shared_init_attributes() {
   return cudaFuncSetAttribute(shared_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
 }
@@ -763,7 +771,16 @@ cudaError_t launch_shared(const SharedArgs& a, int nsm, cudaStream_t st) {
     if (a.timing_stop) cudaEventRecord(a.timing_stop, st);
   }
   if (a.k > 0 && a.ncurves > 0) {
-    shared_topk_kernel<<<(unsigned)a.ncurves, kShTopkThreads, 0, st>>>(a);
+    DenseTopk32Args t{};
+  t.S32 = a.S32;
+  t.nfreq = a.nfreq;
+  t.k = a.k;
+  t.peak_raw = a.peak_raw;
+  t.curve_bad = a.curve_bad;
+  t.status = a.status;
+  t.topk_idx = a.topk_idx;
+  t.topk_S = a.topk_S;
+  dense_topk32_kernel<<<(unsigned)a.ncurves, kShTopkThreads, 0, st>>>(t);
     e = cudaGetLastError();
   }
   return e;

@@ -39,6 +39,53 @@ struct SharedArgs {
   cudaEvent_t timing_stop;
 };
 
+// Per-curve top-k peaks of a dense FP32 periodogram [ncurves][nfreq] (one block per curve).
+struct DenseTopk32Args {
+  const float* S32;
+  int64_t nfreq;
+  int k;
+  int peak_raw;
+  const uint8_t* curve_bad;  // [ncurves]: no peaks for a bad curve
+  const unsigned* status;    // kStatusGrid: no peaks at all
+  int32_t* topk_idx;         // [ncurves][k]
+  float* topk_S;
+};
+cudaError_t launch_dense_topk32(const DenseTopk32Args& t, int64_t ncurves, cudaStream_t st);
+
+// Baseline-drift statistic for a ragged batch (fpw_drift.cu).
+struct DriftArgs {
+  const int64_t* offsets;   // [ncurves + 1]
+  int64_t ncurves;
+  const double* t;
+  const double* x;
+  const double* sigma;
+  const double* freqs;
+  int64_t nfreq;
+  int M;
+  int K;                    // Chebyshev basis functions (0..4)
+  double beta;              // prior standard deviation of each basis coefficient
+  double inv_alpha2;
+  float* payload;           // [nobs][6]: w x, w, w B_0..B_3
+  double* H0;               // [ncurves][4][4]: I + B^T D B
+  double* g;                // [ncurves][4]: H0^-1 B^T D x
+  uint8_t* curve_bad;       // [ncurves]
+  unsigned* status;
+  float* S32;               // dense [ncurves][nfreq] (required when k > 0), or NULL
+  double* S_out;            // dense [ncurves][nfreq] or NULL
+  int k;
+  int peak_raw;
+  int32_t* topk_idx;
+  float* topk_S;
+  cudaEvent_t timing_start;
+  cudaEvent_t timing_stop;
+};
+int drift_threads(int M, int K, int smem_optin);  // threads per block, 0 if M is too large
+size_t drift_smem_bytes(int M, int K, int T);
+int drift_max_basis();
+int drift_payload_floats();
+cudaError_t drift_init_attributes(int max_smem);
+cudaError_t launch_drift(const DriftArgs& a, int T, cudaStream_t st);
+
 size_t shared_image_bytes(int64_t ncurves, int64_t n);
 int shared_curves_per_group();
 int shared_freqs_per_mma(int M, int* n_mma);  // 0 if M is unsupported

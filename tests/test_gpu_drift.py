@@ -1,0 +1,101 @@
+"""The baseline-drift statistic (Appendix A.1-A.2) on the GPU against the dense
+oracle: ragged batches with empty and one-observation curves, tile tails,
+K = 0..4 basis functions, finite and infinite alpha, invalid curves, the
+no-baseline limit against the batched Eq. 1 path, and rejected arguments."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import lightcurves as L
+import oracle
+from gpu_util import assert_S_close, check_topk, run_batch, s_bound, to_dev
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2502_00243_gb300 as G_
+    return G_
+
+
+@pytest.fixture(scope="module")
+def ctx(G):
+    c = G.Context(0)
+    yield c
+    c.close()
+
+
+def run_drift(G, ctx, w, M, K, beta, k, params=None, dense=True):
+    d = to_dev(w)
+    C, F = w.ncurves, w.nfreq
+    idx = torch.empty(max(C * k, 1), dtype=torch.int32, device="cuda")
+    S = torch.empty(max(C * k, 1), dtype=torch.float32, device="cuda")
+    Sd = torch.empty(C * F, dtype=torch.float64, device="cuda") if dense else None
+    G.fpw_periodogram_drift(ctx, None, params, d["offsets"], d["t"], d["x"], d["sigma"], d["freqs"], M, K, beta, k,
+                            idx if k else None, S if k else None, Sd)
+    torch.cuda.synchronize()
+    st = ctx.status()
+    return (idx.cpu().numpy()[:C * k].reshape(C, k), S.cpu().numpy()[:C * k].reshape(C, k),
+            Sd.cpu().numpy().reshape(C, F) if dense else None, st)
+
+
+CASES = [  # (ns, F, M, K, beta, inv_alpha2)
+    ([0, 1, 40, 230, 300], 517, 20, 3, 1.0, 0.0),
+    ([120, 250], 300, 7, 1, 2.0, 0.3),
+    ([200, 64], 260, 12, 4, 0.5, 0.0),
+    ([150], 129, 50, 2, 1.0, 1.0),
+    ([90, 180], 400, 10, 0, 1.0, 0.0),
+]
+
+
+@pytest.mark.parametrize("ns,F,M,K,beta,ia2", CASES)
+def test_drift_dense_and_topk_against_oracle(G, ctx, ns, F, M, K, beta, ia2):
+    w = L.ragged(300 + M + K, ns, F, M=M, k=5)
+    k = 5
+    idx, Sk, Sd, st = run_drift(G, ctx, w, M, K, beta, k, params=G.fpw_params_default(inv_alpha2=ia2))
+    assert st == 0
+    for c in range(w.ncurves):
+        t, x, s = w.curve(c)
+        S_or = oracle.fpw_drift(t, x, s, w.freqs, M, K, beta, ia2)
+        bound = s_bound(x, s)
+        near = oracle.min_edge(t, w.freqs, M) <= 1e-9 if t.size else np.zeros(F, bool)
+        assert_S_close(Sd[c], S_or, bound, mask=~near, what=f"drift M={M} K={K} curve {c} (n={t.size})")
+        o_idx, o_S = oracle.topk(S_or, k + 4)
+        check_topk(idx[c], Sk[c], o_idx, o_S, abs_tol=1e-7 * max(bound, 1e-30), o_dense=S_or,
+                   what=f"drift curve {c} peaks")
+
+
+def test_drift_without_basis_matches_batched_path(G, ctx):
+    w = L.ragged(310, [400, 150, 700], 2000, M=20, k=5)
+    _, _, Sd, st = run_drift(G, ctx, w, 20, 0, 1.0, 0)
+    assert st == 0
+    _, _, Sb, st = run_batch(ctx, w, k=0, dense=True)
+    assert st == 0
+    for c in range(w.ncurves):
+        t, x, s = w.curve(c)
+        assert_S_close(Sd[c], Sb[c], s_bound(x, s), rel=2e-4, what=f"K=0 curve {c}")
+
+
+def test_drift_invalid_curve_and_arguments(G, ctx):
+    w = L.ragged(311, [60, 80, 50], 200, M=10, k=3)
+    w.sigma = w.sigma.copy()
+    w.sigma[w.offsets[1] + 3] = -1.0
+    idx, Sk, Sd, st = run_drift(G, ctx, w, 10, 2, 1.0, 3)
+    assert st == G.FPW_EDATA
+    assert np.isnan(Sd[1]).all() and np.all(idx[1] == -1)
+    for c in (0, 2):
+        t, x, s = w.curve(c)
+        S_or = oracle.fpw_drift(t, x, s, w.freqs, 10, 2, 1.0)
+        assert_S_close(Sd[c], S_or, s_bound(x, s), mask=~(oracle.min_edge(t, w.freqs, 10) <= 1e-9),
+                       what=f"neighbour {c}")
+    with pytest.raises(G.FPWError) as ei:
+        run_drift(G, ctx, w, 10, 5, 1.0, 3)
+    assert ei.value.code == G.FPW_EINVAL
+    with pytest.raises(G.FPWError) as ei:
+        run_drift(G, ctx, w, 10, 2, 1.0, 3, params=G.fpw_params_default(accum=1))
+    assert ei.value.code == G.FPW_ENOTSUP
