@@ -585,6 +585,30 @@ def run_configs(args):
             "batched_path_same_curves_evals_per_s_call": tile_rate,
             "batched_path_same_curves_evals_per_s_tile_kernel": tile_kern}
     print(json.dumps(line), flush=True)
+
+    # baseline drift marginalised (K = 3 Chebyshev terms, beta = 1) on the ragged batch
+    w = L.make("ragged_10k")
+    d = [torch.from_numpy(a).cuda() for a in (w.offsets, w.t, w.x, w.sigma, w.freqs)]
+    idx = torch.empty(w.ncurves * w.k, dtype=torch.int32, device="cuda")
+    Sk = torch.empty(w.ncurves * w.k, dtype=torch.float32, device="cuda")
+    call = lambda: G.fpw_periodogram_drift(ctx, None, None, d[0], d[1], d[2], d[3], d[4], w.M, 3, 1.0, w.k, idx, Sk)
+    call()
+    torch.cuda.synchronize()
+    ctx.set_timing(True)
+    ctx.kernel_time()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    call()
+    e1.record()
+    torch.cuda.synchronize()
+    kms, nl = ctx.kernel_time()
+    ctx.set_timing(False)
+    ev = float(w.offsets[-1]) * w.nfreq
+    print(json.dumps({"config": "ragged_10k, baseline drift marginalised (K=3 Chebyshev terms, beta=1), M=20, top-5",
+                      "evals": ev, "ms_per_call": e0.elapsed_time(e1), "evals_per_s_call": ev / (e0.elapsed_time(e1) / 1e3),
+                      "evals_per_s_drift_kernel": ev / (kms / nl / 1e3),
+                      "smem_roof_evals_per_s": peak * 16.0 / (8.0 * (2 + 3)),
+                      "note": "(2 + K) x 8 B shared-memory read-modify-write per evaluation"}), flush=True)
     ctx.close()
     return 0
 

@@ -99,3 +99,28 @@ def test_drift_invalid_curve_and_arguments(G, ctx):
     with pytest.raises(G.FPWError) as ei:
         run_drift(G, ctx, w, 10, 2, 1.0, 3, params=G.fpw_params_default(accum=1))
     assert ei.value.code == G.FPW_ENOTSUP
+
+
+def test_drift_ragged_10k_full_size_sampled(G, ctx):
+    """All 10^4 curves of the ragged workload with K = 3 (beta = 1), top-5 per
+    curve as the benchmark launches it; for sampled curves the oracle evaluates
+    the reported peaks and their neighbours one frequency at a time."""
+    w = L.make("ragged_10k")
+    idx, Sk, _, st = run_drift(G, ctx, w, 20, 3, 1.0, 5, dense=False)
+    assert st == 0
+    sample = np.random.default_rng(12).choice(w.ncurves, 6, replace=False)
+    for c in sample:
+        t, x, s = w.curve(c)
+        bound = s_bound(x, s)
+        for j in range(5):
+            fi = int(idx[c, j])
+            assert 0 <= fi < w.nfreq
+            nb = np.arange(max(fi - 1, 0), min(fi + 2, w.nfreq))
+            So = oracle.fpw_drift(t, x, s, w.freqs[nb], 20, 3, 1.0)
+            near = oracle.min_edge(t, w.freqs[nb], 20) <= 1e-9
+            Sc = So[list(nb).index(fi)]
+            if not near[list(nb).index(fi)]:
+                assert abs(Sk[c, j] - Sc) <= 1e-4 * abs(Sc) + 1e-7 * bound, (c, j, Sk[c, j], Sc)
+            # a local maximum of the oracle's periodogram up to the FP32 tolerance
+            assert np.all(Sc >= So - (2e-4 * np.abs(So) + 2e-7 * bound)), (c, fi, So)
+        assert np.all(np.diff(Sk[c]) <= 1e-4 * np.abs(Sk[c][:-1]) + 1e-7 * bound)  # ranked by S
