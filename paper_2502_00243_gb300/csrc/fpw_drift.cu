@@ -18,7 +18,7 @@
 //
 // Bins with no observation and 1/alpha^2 = 0 are dropped (their rows vanish).
 // The sums accumulate in FP32 in thread-private shared-memory bins (one thread
-// per frequency, (2 + K) floats per bin), phases are the exact 64-bit anchors
+// per frequency, (2 + K) floats per bin, packed), phases are the exact 64-bit anchors
 // of the tile kernels stepped across a tile of frequencies; the per-frequency
 // reduction and the K x K Cholesky solve run in binary64.
 #include <math.h>
@@ -176,16 +176,21 @@ __global__ void __launch_bounds__(256) drift_prep_kernel(const DriftArgs a) {
 }
 
 // One block per (tile of T frequencies, curve); thread = frequency. Bins
-// [(2 + K) * M][T] floats, thread-private (bank = lane).
+// thread-private (bank = lane): (Y, Bw) as float2 [M][T] and, for K > 0, the
+// K sums w B_k as float4 [M][T]: two packed read-modify-writes per evaluation,
+// loads issued before stores.
+template <int K>
 __global__ void __launch_bounds__(128) drift_kernel(const DriftArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int T = blockDim.x, tid = threadIdx.x;
-  const int K = a.K, M = a.M, NP = 2 + K;
+  const int M = a.M;
   const int64_t c = blockIdx.y, F = a.nfreq;
   const int64_t f0 = (int64_t)blockIdx.x * T, k = f0 + tid;
-  float* bins = reinterpret_cast<float*>(smem);                       // [NP * M][T]
-  unsigned long long* sPD = reinterpret_cast<unsigned long long*>(bins + (size_t)NP * M * T);  // [chunk][2]
-  float* sPay = reinterpret_cast<float*>(sPD + 2 * kDrChunk);         // [chunk][kDrPay]
+  float2* bYB = reinterpret_cast<float2*>(smem);                               // [M][T]
+  float4* bQ = reinterpret_cast<float4*>(bYB + (size_t)M * T);                  // [M][T] (K > 0)
+  ulonglong2* sPD = reinterpret_cast<ulonglong2*>(bQ + (K > 0 ? (size_t)M * T : 0));  // [chunk]
+  float2* sYB = reinterpret_cast<float2*>(sPD + kDrChunk);                      // [chunk]
+  float4* sQ = reinterpret_cast<float4*>(sYB + kDrChunk);                       // [chunk]
   const bool grid_bad = (*(volatile unsigned*)a.status & kStatusGrid) != 0u;
   if (grid_bad) return;
   const bool cbad = a.curve_bad[c] != 0;
@@ -205,28 +210,40 @@ __global__ void __launch_bounds__(128) drift_kernel(const DriftArgs a) {
   const double fk = k < F ? a.freqs[k] : fa;
   const bool nonlin = k < F && fabs(fk - fma((double)tid, df, fa)) * tm > kGridTolCycles;
   const bool lin = !__syncthreads_or(nonlin);
-  for (int q = 0; q < NP * M; ++q) bins[q * T + tid] = 0.f;
+  for (int m = 0; m < M; ++m) {
+    bYB[m * T + tid] = make_float2(0.f, 0.f);
+    if (K > 0) bQ[m * T + tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
   for (int64_t oc = 0; oc < n; oc += kDrChunk) {
     const int cnt = (int)((n - oc) < kDrChunk ? (n - oc) : kDrChunk);
     __syncthreads();
     for (int i = tid; i < cnt; i += T) {
       const double ti = a.t[o0 + oc + i];
-      sPD[2 * i] = lin ? phase_fixed64(ti, fa) : (unsigned long long)__double_as_longlong(ti);
-      sPD[2 * i + 1] = lin ? phase_fixed64(ti, df) : 0ull;
+      sPD[i] = lin ? make_ulonglong2(phase_fixed64(ti, fa), phase_fixed64(ti, df))
+                   : make_ulonglong2((unsigned long long)__double_as_longlong(ti), 0ull);
       const float* pay = a.payload + (size_t)(o0 + oc + i) * kDrPay;
-#pragma unroll
-      for (int q = 0; q < kDrPay; ++q) sPay[i * kDrPay + q] = pay[q];
+      sYB[i] = make_float2(pay[0], pay[1]);
+      if (K > 0) sQ[i] = make_float4(pay[2], pay[3], pay[4], pay[5]);
     }
     __syncthreads();
     if (!cbad) {
+      float2* const yb = bYB + tid;
+      float4* const qb = bQ + tid;
+#pragma unroll 2
       for (int i = 0; i < cnt; ++i) {
-        const unsigned long long P = sPD[2 * i], D = sPD[2 * i + 1];
+        const ulonglong2 pd = sPD[i];
         const unsigned long long phi =
-            lin ? P + (unsigned long long)tid * D : phase_fixed64(__longlong_as_double((long long)P), fk);
-        const int m = (int)bin_of_phase(phi, (unsigned)M);
-        float* b = bins + (size_t)m * T + tid;
-        const float* pay = sPay + i * kDrPay;
-        for (int q = 0; q < NP; ++q) b[(size_t)q * M * T] += pay[q];
+            lin ? pd.x + (unsigned long long)tid * pd.y : phase_fixed64(__longlong_as_double((long long)pd.x), fk);
+        const int mT = (int)bin_of_phase(phi, (unsigned)M) * T;
+        const float2 p2 = sYB[i];
+        const float2 v2 = yb[mT];
+        float4 v4;
+        if (K > 0) v4 = qb[mT];
+        yb[mT] = make_float2(v2.x + p2.x, v2.y + p2.y);
+        if (K > 0) {
+          const float4 p4 = sQ[i];
+          qb[mT] = make_float4(v4.x + p4.x, v4.y + p4.y, v4.z + p4.z, v4.w + p4.w);
+        }
       }
     }
   }
@@ -234,41 +251,54 @@ __global__ void __launch_bounds__(128) drift_kernel(const DriftArgs a) {
   // binary64 reduction: S = sum z^2 / L + v^T H^-1 v
   double H[kDrMaxK][kDrMaxK], v[kDrMaxK], g[kDrMaxK];
   const double* h0 = a.H0 + c * kDrMaxK * kDrMaxK;
+#pragma unroll
   for (int p = 0; p < K; ++p) {
     g[p] = a.g[c * kDrMaxK + p];
     v[p] = 0.0;
+#pragma unroll
     for (int q = 0; q < K; ++q) H[p][q] = h0[p * kDrMaxK + q];
   }
   const double cal = a.inv_alpha2;
   double S = 0.0;
   for (int m = 0; m < M; ++m) {
-    const double Y = bins[(size_t)(0 * M + m) * T + tid];
-    const double Bw = bins[(size_t)(1 * M + m) * T + tid];
-    const double L = Bw + cal;
+    const float2 yb = bYB[m * T + tid];
+    const double L = (double)yb.y + cal;
     if (!(L > 0.0)) continue;  // empty bin with 1/alpha^2 = 0: dropped
     double Q[kDrMaxK];
-    double z = Y;
-    for (int p = 0; p < K; ++p) {
-      Q[p] = bins[(size_t)((2 + p) * M + m) * T + tid];
-      z -= Q[p] * g[p];
+    double z = yb.x;
+    if (K > 0) {
+      const float4 q4 = bQ[m * T + tid];
+      const float qq[4] = {q4.x, q4.y, q4.z, q4.w};
+#pragma unroll
+      for (int p = 0; p < K; ++p) {
+        Q[p] = qq[p];
+        z -= Q[p] * g[p];
+      }
     }
     const double zl = z / L;
     S += z * zl;
+#pragma unroll
     for (int p = 0; p < K; ++p) {
       v[p] += Q[p] * zl;
+#pragma unroll
       for (int q = 0; q < K; ++q) H[p][q] -= Q[p] * Q[q] / L;
     }
   }
   // v^T H^-1 v by Cholesky (H >= I)
   double Lc[kDrMaxK][kDrMaxK], y[kDrMaxK];
+#pragma unroll
   for (int p = 0; p < K; ++p)
+#pragma unroll
     for (int q = 0; q <= p; ++q) {
       double s = H[p][q];
+#pragma unroll
       for (int r = 0; r < q; ++r) s -= Lc[p][r] * Lc[q][r];
       Lc[p][q] = (p == q) ? sqrt(s > 0.0 ? s : 0.0) : s / Lc[q][q];
     }
+#pragma unroll
   for (int p = 0; p < K; ++p) {
     double s = v[p];
+#pragma unroll
     for (int r = 0; r < p; ++r) s -= Lc[p][r] * y[r];
     y[p] = Lc[p][p] > 0.0 ? s / Lc[p][p] : 0.0;
     S += y[p] * y[p];
@@ -278,13 +308,23 @@ __global__ void __launch_bounds__(128) drift_kernel(const DriftArgs a) {
   if (a.S_out) a.S_out[c * F + k] = cbad ? (double)Sf : S;
 }
 
+const void* drift_fn(int K) {
+  switch (K) {
+    case 0: return reinterpret_cast<const void*>(&drift_kernel<0>);
+    case 1: return reinterpret_cast<const void*>(&drift_kernel<1>);
+    case 2: return reinterpret_cast<const void*>(&drift_kernel<2>);
+    case 3: return reinterpret_cast<const void*>(&drift_kernel<3>);
+    default: return reinterpret_cast<const void*>(&drift_kernel<4>);
+  }
+}
+
 }  // namespace
 
 // Dynamic shared memory the drift kernel may use: the opt-in limit minus its
 // static shared memory.
 static size_t drift_dynamic_limit(int smem_optin) {
   cudaFuncAttributes fa{};
-  if (cudaFuncGetAttributes(&fa, drift_kernel) != cudaSuccess) return 0;
+  if (cudaFuncGetAttributes(&fa, drift_fn(4)) != cudaSuccess) return 0;
   return smem_optin > (int)fa.sharedSizeBytes ? (size_t)(smem_optin - (int)fa.sharedSizeBytes) : 0;
 }
 
@@ -296,7 +336,7 @@ int drift_threads(int M, int K, int smem_optin) {
 }
 
 size_t drift_smem_bytes(int M, int K, int T) {
-  return (size_t)(2 + K) * M * T * 4 + (size_t)kDrChunk * 16 + (size_t)kDrChunk * kDrPay * 4;
+  return (size_t)M * T * (K > 0 ? 24 : 8) + (size_t)kDrChunk * (16 + 8 + 16);
 }
 
 int drift_max_basis() { return kDrMaxK; }
@@ -304,8 +344,12 @@ int drift_max_basis() { return kDrMaxK; }
 int drift_payload_floats() { return kDrPay; }
 
 cudaError_t drift_init_attributes(int max_smem) {
-  return cudaFuncSetAttribute(drift_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)drift_dynamic_limit(max_smem));
+  const int lim = (int)drift_dynamic_limit(max_smem);
+  for (int K = 0; K <= kDrMaxK; ++K) {
+    const cudaError_t e = cudaFuncSetAttribute(drift_fn(K), cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_drift(const DriftArgs& a, int T, cudaStream_t st) {
@@ -315,8 +359,9 @@ cudaError_t launch_drift(const DriftArgs& a, int T, cudaStream_t st) {
   if (e != cudaSuccess || a.nfreq <= 0) return e;
   const int64_t tiles = (a.nfreq + T - 1) / T;
   if (a.timing_start) cudaEventRecord(a.timing_start, st);
-  drift_kernel<<<dim3((unsigned)tiles, (unsigned)a.ncurves), T, drift_smem_bytes(a.M, a.K, T), st>>>(a);
-  e = cudaGetLastError();
+  void* params[] = {const_cast<DriftArgs*>(&a)};
+  e = cudaLaunchKernel(drift_fn(a.K), dim3((unsigned)tiles, (unsigned)a.ncurves), dim3(T), params,
+                       drift_smem_bytes(a.M, a.K, T), st);
   if (e != cudaSuccess) return e;
   if (a.timing_stop) cudaEventRecord(a.timing_stop, st);
   if (a.k > 0) {
