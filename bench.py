@@ -613,6 +613,51 @@ def run_configs(args):
     return 0
 
 
+def run_case(args):
+    """One small call of the shared-timestamp or the baseline-drift path, for
+    profiling: two untimed calls, then one call timed with the library's
+    kernel-timing hook; prints one JSON line."""
+    import numpy as np
+    import torch
+
+    import lightcurves as L
+    import paper_2502_00243_gb300 as G
+    torch.cuda.set_device(0)
+    ctx = G.Context(0)
+    C, F = args.case_curves, args.nfreq
+    idx = torch.empty(C * 5, dtype=torch.int32, device="cuda")
+    Sk = torch.empty(C * 5, dtype=torch.float32, device="cuda")
+    if args.case == "shared":
+        w = L.make("shared_4096", range(C))
+        n = L.SHARED_N
+        freqs = np.linspace(0.01, 50.0, F)
+        d = [torch.from_numpy(np.ascontiguousarray(a)).cuda()
+             for a in (w.t[:n], w.x.reshape(C, n), w.sigma.reshape(C, n), freqs)]
+        call = lambda: G.fpw_periodogram_shared(ctx, None, None, d[0], d[1], d[2], d[3], 20, 5, idx, Sk)
+        ev = float(C) * n * F
+        what = f"shared_4096: {C} curves sharing N={n} times, M=20, {F} freqs 0.01-50 1/d, top-5"
+    else:
+        w = L.make("ragged_10k", range(C), nfreq=F)
+        d = [torch.from_numpy(a).cuda() for a in (w.offsets, w.t, w.x, w.sigma, w.freqs)]
+        call = lambda: G.fpw_periodogram_drift(ctx, None, None, d[0], d[1], d[2], d[3], d[4], 20, 3, 1.0, 5, idx, Sk)
+        ev = float(w.offsets[-1]) * F
+        what = f"ragged_10k: first {C} curves, baseline drift K=3 beta=1, M=20, {F} freqs 0.02-50 1/d, top-5"
+    call()
+    call()
+    torch.cuda.synchronize()
+    ctx.set_timing(True)
+    ctx.kernel_time()
+    call()
+    torch.cuda.synchronize()
+    kms, nl = ctx.kernel_time()
+    ctx.set_timing(False)
+    st = ctx.status()
+    print(json.dumps({"case": args.case, "config": what, "status": st, "kernel_ms": kms / max(nl, 1),
+                      "evals": ev, "evals_per_s_kernel": ev / (kms / max(nl, 1) / 1e3)}), flush=True)
+    ctx.close()
+    return 0 if st == 0 else 1
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -633,6 +678,8 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--autotune", action="store_true", help="measure and install tuned kernel shapes before timing")
     ap.add_argument("--configs", action="store_true", help="report every workload (one JSON line each) instead")
+    ap.add_argument("--case", choices=["shared", "drift"], help="one small call of that path (profiling case)")
+    ap.add_argument("--case-curves", type=int, default=256)
     args = ap.parse_args(argv)
     if args.warmup < 0 or args.steps < 1:
         ap.error("need --steps >= 1 and --warmup >= 0")
@@ -640,6 +687,8 @@ def main(argv=None):
         return run_reference(args)
     if args.configs:
         return run_configs(args)
+    if args.case:
+        return run_case(args)
     return run_gb300(args)
 
 
