@@ -229,19 +229,43 @@ __global__ void __launch_bounds__(128) drift_kernel(const DriftArgs a) {
     if (!cbad) {
       float2* const yb = bYB + tid;
       float4* const qb = bQ + tid;
-#pragma unroll 2
-      for (int i = 0; i < cnt; ++i) {
-        const ulonglong2 pd = sPD[i];
+      auto bin_T = [&](const ulonglong2 pd) {
         const unsigned long long phi =
             lin ? pd.x + (unsigned long long)tid * pd.y : phase_fixed64(__longlong_as_double((long long)pd.x), fk);
-        const int mT = (int)bin_of_phase(phi, (unsigned)M) * T;
+        return (int)bin_of_phase(phi, (unsigned)M) * T;
+      };
+      // two observations per iteration: both read-modify-write chains are in
+      // flight at once; where both fall in one bin the second update starts
+      // from the first one's sum (same additions in the same order)
+      int i = 0;
+      for (; i + 1 < cnt; i += 2) {
+        const int ma = bin_T(sPD[i]), mb = bin_T(sPD[i + 1]);
+        const float2 pa = sYB[i], pb = sYB[i + 1];
+        float2 va = yb[ma], vb = yb[mb];
+        float4 qa, qbv;
+        if (K > 0) {
+          qa = qb[ma];
+          qbv = qb[mb];
+        }
+        const float2 ua = make_float2(va.x + pa.x, va.y + pa.y);
+        if (ma == mb) vb = ua;
+        yb[ma] = ua;
+        yb[mb] = make_float2(vb.x + pb.x, vb.y + pb.y);
+        if (K > 0) {
+          const float4 ra = sQ[i], rb = sQ[i + 1];
+          const float4 wa = make_float4(qa.x + ra.x, qa.y + ra.y, qa.z + ra.z, qa.w + ra.w);
+          if (ma == mb) qbv = wa;
+          qb[ma] = wa;
+          qb[mb] = make_float4(qbv.x + rb.x, qbv.y + rb.y, qbv.z + rb.z, qbv.w + rb.w);
+        }
+      }
+      if (i < cnt) {
+        const int mT = bin_T(sPD[i]);
         const float2 p2 = sYB[i];
         const float2 v2 = yb[mT];
-        float4 v4;
-        if (K > 0) v4 = qb[mT];
         yb[mT] = make_float2(v2.x + p2.x, v2.y + p2.y);
         if (K > 0) {
-          const float4 p4 = sQ[i];
+          const float4 v4 = qb[mT], p4 = sQ[i];
           qb[mT] = make_float4(v4.x + p4.x, v4.y + p4.y, v4.z + p4.z, v4.w + p4.w);
         }
       }
