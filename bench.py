@@ -607,8 +607,9 @@ def run_configs(args):
     print(json.dumps({"config": "ragged_10k, baseline drift marginalised (K=3 Chebyshev terms, beta=1), M=20, top-5",
                       "evals": ev, "ms_per_call": e0.elapsed_time(e1), "evals_per_s_call": ev / (e0.elapsed_time(e1) / 1e3),
                       "evals_per_s_drift_kernel": ev / (kms / nl / 1e3),
-                      "smem_roof_evals_per_s": peak * 16.0 / (8.0 * (2 + 3)),
-                      "note": "(2 + K) x 8 B shared-memory read-modify-write per evaluation"}), flush=True)
+                      "smem_roof_evals_per_s": peak * 16.0 / 32.0,
+                      "roofline_frac": ev / (kms / nl / 1e3) / (peak * 16.0 / 32.0),
+                      "note": "K=3: one (Y, Bw, Q_1, Q_2) float4 read-modify-write (2 x 16 B) per evaluation"}), flush=True)
     ctx.close()
     return 0
 

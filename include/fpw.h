@@ -200,10 +200,12 @@ FPW_API int fpw_periodogram_shared(fpw_ctx* ctx, void* stream, const fpw_params*
  *       fpw_periodogram_batch_ex (device pointers; ncurves <= 65535)
  *   K: 0..4 basis functions; beta >= 0: prior standard deviation of each
  *       basis coefficient, in flux units
- *   M: 1 <= M, with (2 + K) * M * 32 * 4 bytes of shared memory at most
- *       (FPW_ENOTSUP beyond)
+ *   M: 1 <= M, with 32 M b + 128 * 36 bytes within the device's shared
+ *       memory per block, b = 8 (K <= 1), 16 (K = 2, 3) or 20 (K = 4) bytes
+ *       per bin (FPW_ENOTSUP beyond)
  * params: FPW_PHASE_FIXED64 and FPW_ACCUM_FP32 only; inv_alpha2 and
- * peak_mode apply. Scratch held by the context: 24 bytes per observation and,
+ * peak_mode apply. Scratch held by the context: 32 bytes per observation,
+ * 168 bytes per curve and,
  * when k > 0, a dense FP32 periodogram of 4 ncurves nfreq bytes. Reads
  * offsets[ncurves] back to the host (synchronizes `stream` once).
  * Errors: FPW_EINVAL, FPW_ENOTSUP, FPW_ENOMEM, FPW_ECUDA; invalid data in a

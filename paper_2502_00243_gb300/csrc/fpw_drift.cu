@@ -17,10 +17,13 @@
 //   H = H0 - sum_m Q_m Q_m^T / L_m   (symmetric positive definite, >= I).
 //
 // Bins with no observation and 1/alpha^2 = 0 are dropped (their rows vanish).
+// B_0 = beta T_0 = beta is constant, so Q_m0 = beta Bw_m needs no sum of its
+// own: a bin holds Y, Bw and Q_m1..Q_m(K-1), 1 + max(K, 1) floats.
 // The sums accumulate in FP32 in thread-private shared-memory bins (one thread
-// per frequency, (2 + K) floats per bin, packed), phases are the exact 64-bit anchors
-// of the tile kernels stepped across a tile of frequencies; the per-frequency
-// reduction and the K x K Cholesky solve run in binary64.
+// per frequency, packed as float2 / float4 / float4 + float), phases are the
+// exact 64-bit anchors of the tile kernels stepped across a tile of
+// frequencies; the per-frequency reduction (one reciprocal per bin, the lower
+// triangle of the symmetric H) and the K x K Cholesky solve run in binary64.
 #include <math.h>
 
 #include "fpw_shared.cuh"
@@ -29,8 +32,22 @@ namespace fpw {
 namespace {
 
 constexpr int kDrMaxK = 4;
-constexpr int kDrPay = 2 + kDrMaxK;  // payload floats per observation: w x, w, w B_0..B_{K-1}
-constexpr int kDrChunk = 256;        // observations staged at a time
+constexpr int kDrChunk = 128;  // observations staged at a time
+
+// Per observation, written once by the prep kernel.
+struct DriftObs {
+  float4 q;                // w x, w, w B_1, w B_2
+  unsigned long long D;    // frac(t df) as 64-bit fixed point (linear grids)
+  float q3;                // w B_3
+  float pad;
+};
+static_assert(sizeof(DriftObs) == 32, "32-byte records");
+
+// Bytes of the staged copy of one observation: {Phi, D}, q and, for K = 4, q3.
+__host__ __device__ constexpr int drift_stage_bytes(int K) { return 16 + 16 + (K > 3 ? 4 : 0); }
+// Bytes of one (frequency, bin) slot: (Y, Bw), then Q_1, Q_2 in the same
+// float4 for K = 2, 3, and Q_3 in a float of its own for K = 4.
+__host__ __device__ constexpr int drift_bin_bytes(int K) { return K <= 1 ? 8 : (K <= 3 ? 16 : 20); }
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -79,6 +96,7 @@ __global__ void __launch_bounds__(256) drift_prep_kernel(const DriftArgs a) {
     }
     tl[0] = a0;
     tl[1] = a1;
+    a.tabs[c] = (a1 >= a0) ? fmax(fabs(a0), fabs(a1)) : 0.0;  // max |t| (0 with no finite time)
     a.curve_bad[c] = b > 0.0 ? 1 : 0;
     if (b > 0.0) atomicOr(a.status, kStatusData);
   }
@@ -89,8 +107,9 @@ __global__ void __launch_bounds__(256) drift_prep_kernel(const DriftArgs a) {
   double acc[kDrMaxK * kDrMaxK + kDrMaxK];
 #pragma unroll
   for (int q = 0; q < kDrMaxK * kDrMaxK + kDrMaxK; ++q) acc[q] = 0.0;
+  const double df = (a.nfreq > 1) ? (a.freqs[a.nfreq - 1] - a.freqs[0]) / (double)(a.nfreq - 1) : 0.0;
   for (int64_t i = tid; i < n; i += blockDim.x) {
-    float* pay = a.payload + (size_t)(o0 + i) * kDrPay;
+    DriftObs* const pay = reinterpret_cast<DriftObs*>(a.payload) + (o0 + i);
     double w = 0.0, x = 0.0;
     if (!cbad) {
       const double s = a.sigma[o0 + i];
@@ -115,11 +134,10 @@ __global__ void __launch_bounds__(256) drift_prep_kernel(const DriftArgs a) {
       }
       Bk[k] = a.beta * T;
     }
-    pay[0] = (float)(w * x);
-    pay[1] = (float)w;
+    float wb[kDrMaxK];
 #pragma unroll
     for (int k = 0; k < kDrMaxK; ++k) {
-      pay[2 + k] = k < K ? (float)(w * Bk[k]) : 0.f;
+      wb[k] = k < K ? (float)(w * Bk[k]) : 0.f;
       if (k < K) {
 #pragma unroll
         for (int l = 0; l < kDrMaxK; ++l)
@@ -127,6 +145,12 @@ __global__ void __launch_bounds__(256) drift_prep_kernel(const DriftArgs a) {
         acc[kDrMaxK * kDrMaxK + k] += w * Bk[k] * x;
       }
     }
+    DriftObs ob;
+    ob.q = make_float4((float)(w * x), (float)w, wb[1], wb[2]);
+    ob.D = isfinite(a.t[o0 + i]) ? phase_fixed64(a.t[o0 + i], df) : 0ull;
+    ob.q3 = wb[3];
+    ob.pad = 0.f;
+    *pay = ob;
   }
   __syncthreads();
 #pragma unroll
@@ -176,21 +200,22 @@ __global__ void __launch_bounds__(256) drift_prep_kernel(const DriftArgs a) {
 }
 
 // One block per (tile of T frequencies, curve); thread = frequency. Bins
-// thread-private (bank = lane): (Y, Bw) as float2 [M][T] and, for K > 0, the
-// K sums w B_k as float4 [M][T]: two packed read-modify-writes per evaluation,
-// loads issued before stores.
+// thread-private (bank = lane), [M][T] slots of drift_bin_bytes(K): one packed
+// read-modify-write per evaluation for K <= 3 (two for K = 4), two
+// observations per iteration with all loads issued before the stores.
 template <int K>
 __global__ void __launch_bounds__(128) drift_kernel(const DriftArgs a) {
+  constexpr bool kWide = K >= 2;  // (Y, Bw, Q_1, Q_2) as float4, else (Y, Bw) as float2
   extern __shared__ __align__(16) unsigned char smem[];
   const int T = blockDim.x, tid = threadIdx.x;
   const int M = a.M;
   const int64_t c = blockIdx.y, F = a.nfreq;
   const int64_t f0 = (int64_t)blockIdx.x * T, k = f0 + tid;
-  float2* bYB = reinterpret_cast<float2*>(smem);                               // [M][T]
-  float4* bQ = reinterpret_cast<float4*>(bYB + (size_t)M * T);                  // [M][T] (K > 0)
-  ulonglong2* sPD = reinterpret_cast<ulonglong2*>(bQ + (K > 0 ? (size_t)M * T : 0));  // [chunk]
-  float2* sYB = reinterpret_cast<float2*>(sPD + kDrChunk);                      // [chunk]
-  float4* sQ = reinterpret_cast<float4*>(sYB + kDrChunk);                       // [chunk]
+  unsigned char* const bins = smem;                                                     // [M][T] main slots
+  float* const bQ3 = reinterpret_cast<float*>(bins + (size_t)M * T * (kWide ? 16 : 8));  // [M][T] (K = 4)
+  ulonglong2* const sPD = reinterpret_cast<ulonglong2*>(smem + (size_t)M * T * drift_bin_bytes(K));  // [chunk]
+  float4* const sQ = reinterpret_cast<float4*>(sPD + kDrChunk);                         // [chunk]
+  float* const sQ3 = reinterpret_cast<float*>(sQ + kDrChunk);                           // [chunk] (K = 4)
   const bool grid_bad = (*(volatile unsigned*)a.status & kStatusGrid) != 0u;
   if (grid_bad) return;
   const bool cbad = a.curve_bad[c] != 0;
@@ -198,81 +223,87 @@ __global__ void __launch_bounds__(128) drift_kernel(const DriftArgs a) {
   const double df = (F > 1) ? (a.freqs[F - 1] - a.freqs[0]) / (double)(F - 1) : 0.0;
   const double fa = a.freqs[f0];
   // linear grid over this tile (the tile kernels' bound on the phase error)?
-  double tm = 0.0;
-  for (int64_t i = tid; i < n; i += T) tm = fmax(tm, fabs(a.t[o0 + i]));
-  __shared__ double s_tm[4];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) tm = fmax(tm, __shfl_xor_sync(0xffffffffu, tm, o));
-  if ((tid & 31) == 0) s_tm[tid >> 5] = tm;
-  __syncthreads();
-  tm = 0.0;
-  for (int q = 0; q < (T >> 5); ++q) tm = fmax(tm, s_tm[q]);
+  const double tm = a.tabs[c];
   const double fk = k < F ? a.freqs[k] : fa;
   const bool nonlin = k < F && fabs(fk - fma((double)tid, df, fa)) * tm > kGridTolCycles;
   const bool lin = !__syncthreads_or(nonlin);
   for (int m = 0; m < M; ++m) {
-    bYB[m * T + tid] = make_float2(0.f, 0.f);
-    if (K > 0) bQ[m * T + tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (kWide)
+      reinterpret_cast<float4*>(bins)[m * T + tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+    else
+      reinterpret_cast<float2*>(bins)[m * T + tid] = make_float2(0.f, 0.f);
+    if (K > 3) bQ3[m * T + tid] = 0.f;
   }
+  const DriftObs* const obs = reinterpret_cast<const DriftObs*>(a.payload) + o0;
   for (int64_t oc = 0; oc < n; oc += kDrChunk) {
     const int cnt = (int)((n - oc) < kDrChunk ? (n - oc) : kDrChunk);
     __syncthreads();
     for (int i = tid; i < cnt; i += T) {
       const double ti = a.t[o0 + oc + i];
-      sPD[i] = lin ? make_ulonglong2(phase_fixed64(ti, fa), phase_fixed64(ti, df))
+      const DriftObs ob = obs[oc + i];
+      sPD[i] = lin ? make_ulonglong2(phase_fixed64(ti, fa), ob.D)
                    : make_ulonglong2((unsigned long long)__double_as_longlong(ti), 0ull);
-      const float* pay = a.payload + (size_t)(o0 + oc + i) * kDrPay;
-      sYB[i] = make_float2(pay[0], pay[1]);
-      if (K > 0) sQ[i] = make_float4(pay[2], pay[3], pay[4], pay[5]);
+      sQ[i] = ob.q;
+      if (K > 3) sQ3[i] = ob.q3;
     }
     __syncthreads();
     if (!cbad) {
-      float2* const yb = bYB + tid;
-      float4* const qb = bQ + tid;
-      auto bin_T = [&](const ulonglong2 pd) {
+      auto slot = [&](const ulonglong2 pd) {
         const unsigned long long phi =
             lin ? pd.x + (unsigned long long)tid * pd.y : phase_fixed64(__longlong_as_double((long long)pd.x), fk);
-        return (int)bin_of_phase(phi, (unsigned)M) * T;
+        return (int)bin_of_phase(phi, (unsigned)M) * T + tid;
       };
       // two observations per iteration: both read-modify-write chains are in
       // flight at once; where both fall in one bin the second update starts
       // from the first one's sum (same additions in the same order)
       int i = 0;
       for (; i + 1 < cnt; i += 2) {
-        const int ma = bin_T(sPD[i]), mb = bin_T(sPD[i + 1]);
-        const float2 pa = sYB[i], pb = sYB[i + 1];
-        float2 va = yb[ma], vb = yb[mb];
-        float4 qa, qbv;
-        if (K > 0) {
-          qa = qb[ma];
-          qbv = qb[mb];
+        const int ma = slot(sPD[i]), mb = slot(sPD[i + 1]);
+        const float4 pa = sQ[i], pb = sQ[i + 1];
+        if (kWide) {
+          float4* const b4 = reinterpret_cast<float4*>(bins);
+          const float4 va = b4[ma];
+          float4 vb = b4[mb];
+          const float4 ua = make_float4(va.x + pa.x, va.y + pa.y, va.z + pa.z, va.w + pa.w);
+          if (ma == mb) vb = ua;
+          b4[ma] = ua;
+          b4[mb] = make_float4(vb.x + pb.x, vb.y + pb.y, vb.z + pb.z, vb.w + pb.w);
+        } else {
+          float2* const b2 = reinterpret_cast<float2*>(bins);
+          const float2 va = b2[ma];
+          float2 vb = b2[mb];
+          const float2 ua = make_float2(va.x + pa.x, va.y + pa.y);
+          if (ma == mb) vb = ua;
+          b2[ma] = ua;
+          b2[mb] = make_float2(vb.x + pb.x, vb.y + pb.y);
         }
-        const float2 ua = make_float2(va.x + pa.x, va.y + pa.y);
-        if (ma == mb) vb = ua;
-        yb[ma] = ua;
-        yb[mb] = make_float2(vb.x + pb.x, vb.y + pb.y);
-        if (K > 0) {
-          const float4 ra = sQ[i], rb = sQ[i + 1];
-          const float4 wa = make_float4(qa.x + ra.x, qa.y + ra.y, qa.z + ra.z, qa.w + ra.w);
-          if (ma == mb) qbv = wa;
-          qb[ma] = wa;
-          qb[mb] = make_float4(qbv.x + rb.x, qbv.y + rb.y, qbv.z + rb.z, qbv.w + rb.w);
+        if (K > 3) {
+          const float qa = bQ3[ma];
+          float qb = bQ3[mb];
+          const float ra = qa + sQ3[i];
+          if (ma == mb) qb = ra;
+          bQ3[ma] = ra;
+          bQ3[mb] = qb + sQ3[i + 1];
         }
       }
       if (i < cnt) {
-        const int mT = bin_T(sPD[i]);
-        const float2 p2 = sYB[i];
-        const float2 v2 = yb[mT];
-        yb[mT] = make_float2(v2.x + p2.x, v2.y + p2.y);
-        if (K > 0) {
-          const float4 v4 = qb[mT], p4 = sQ[i];
-          qb[mT] = make_float4(v4.x + p4.x, v4.y + p4.y, v4.z + p4.z, v4.w + p4.w);
+        const int ma = slot(sPD[i]);
+        const float4 pa = sQ[i];
+        if (kWide) {
+          float4* const b4 = reinterpret_cast<float4*>(bins);
+          const float4 va = b4[ma];
+          b4[ma] = make_float4(va.x + pa.x, va.y + pa.y, va.z + pa.z, va.w + pa.w);
+        } else {
+          float2* const b2 = reinterpret_cast<float2*>(bins);
+          const float2 va = b2[ma];
+          b2[ma] = make_float2(va.x + pa.x, va.y + pa.y);
         }
+        if (K > 3) bQ3[ma] += sQ3[i];
       }
     }
   }
   if (k >= F) return;
-  // binary64 reduction: S = sum z^2 / L + v^T H^-1 v
+  // binary64 reduction: S = sum z^2 / L + v^T H^-1 v, H kept as its lower triangle
   double H[kDrMaxK][kDrMaxK], v[kDrMaxK], g[kDrMaxK];
   const double* h0 = a.H0 + c * kDrMaxK * kDrMaxK;
 #pragma unroll
@@ -280,32 +311,39 @@ __global__ void __launch_bounds__(128) drift_kernel(const DriftArgs a) {
     g[p] = a.g[c * kDrMaxK + p];
     v[p] = 0.0;
 #pragma unroll
-    for (int q = 0; q < K; ++q) H[p][q] = h0[p * kDrMaxK + q];
+    for (int q = 0; q <= p; ++q) H[p][q] = h0[p * kDrMaxK + q];
   }
-  const double cal = a.inv_alpha2;
+  const double cal = a.inv_alpha2, beta = a.beta;
   double S = 0.0;
   for (int m = 0; m < M; ++m) {
-    const float2 yb = bYB[m * T + tid];
-    const double L = (double)yb.y + cal;
-    if (!(L > 0.0)) continue;  // empty bin with 1/alpha^2 = 0: dropped
-    double Q[kDrMaxK];
-    double z = yb.x;
-    if (K > 0) {
-      const float4 q4 = bQ[m * T + tid];
-      const float qq[4] = {q4.x, q4.y, q4.z, q4.w};
-#pragma unroll
-      for (int p = 0; p < K; ++p) {
-        Q[p] = qq[p];
-        z -= Q[p] * g[p];
-      }
+    double Y, Bw, Q[kDrMaxK];
+    if (kWide) {
+      const float4 b = reinterpret_cast<const float4*>(bins)[m * T + tid];
+      Y = b.x;
+      Bw = b.y;
+      Q[1] = b.z;
+      if (K > 2) Q[2] = b.w;
+    } else {
+      const float2 b = reinterpret_cast<const float2*>(bins)[m * T + tid];
+      Y = b.x;
+      Bw = b.y;
     }
-    const double zl = z / L;
+    if (K > 3) Q[3] = bQ3[m * T + tid];
+    const double L = Bw + cal;
+    if (!(L > 0.0)) continue;  // empty bin with 1/alpha^2 = 0: dropped
+    if (K > 0) Q[0] = beta * Bw;
+    const double rL = 1.0 / L;
+    double z = Y;
+#pragma unroll
+    for (int p = 0; p < K; ++p) z -= Q[p] * g[p];
+    const double zl = z * rL;
     S += z * zl;
 #pragma unroll
     for (int p = 0; p < K; ++p) {
       v[p] += Q[p] * zl;
+      const double qs = Q[p] * rL;
 #pragma unroll
-      for (int q = 0; q < K; ++q) H[p][q] -= Q[p] * Q[q] / L;
+      for (int q = 0; q <= p; ++q) H[p][q] -= qs * Q[q];
     }
   }
   // v^T H^-1 v by Cholesky (H >= I)
@@ -360,12 +398,12 @@ int drift_threads(int M, int K, int smem_optin) {
 }
 
 size_t drift_smem_bytes(int M, int K, int T) {
-  return (size_t)M * T * (K > 0 ? 24 : 8) + (size_t)kDrChunk * (16 + 8 + 16);
+  return (size_t)M * T * drift_bin_bytes(K) + (size_t)kDrChunk * drift_stage_bytes(K);
 }
 
 int drift_max_basis() { return kDrMaxK; }
 
-int drift_payload_floats() { return kDrPay; }
+size_t drift_payload_bytes() { return sizeof(DriftObs); }
 
 cudaError_t drift_init_attributes(int max_smem) {
   const int lim = (int)drift_dynamic_limit(max_smem);

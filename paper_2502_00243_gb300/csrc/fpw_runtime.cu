@@ -124,7 +124,7 @@ struct fpw_ctx {
   cudaStream_t own_stream = nullptr;
   DevBuf aw, cand_S, cand_idx, curve_bad, words, dense, tile_dev;
   DevBuf sh_image, sh_scale, sh_S32, sh_step, sh_sink;  // shared-timestamp path scratch
-  DevBuf dr_payload, dr_H0, dr_g;                       // baseline-drift path scratch
+  DevBuf dr_payload, dr_H0, dr_g, dr_tabs;                     // baseline-drift path scratch
   DevBuf h_off, h_t, h_x, h_sigma, h_freqs, h_idx, h_S;  // device copies for the host entry point
   std::vector<int64_t> off_host;                          // host copy of offsets (when not supplied)
   std::vector<Plan*> plans;
@@ -719,7 +719,7 @@ int fpw_ctx_destroy(fpw_ctx* ctx) {
     for (DevBuf* b : {&ctx->aw, &ctx->cand_S, &ctx->cand_idx, &ctx->curve_bad, &ctx->words, &ctx->dense, &ctx->tile_dev, &ctx->h_off,
                       &ctx->h_t, &ctx->h_x, &ctx->h_sigma, &ctx->h_freqs, &ctx->h_idx, &ctx->h_S, &ctx->sh_image,
                       &ctx->sh_scale, &ctx->sh_S32, &ctx->sh_step, &ctx->sh_sink, &ctx->dr_payload,
-                      &ctx->dr_H0, &ctx->dr_g})
+                      &ctx->dr_H0, &ctx->dr_g, &ctx->dr_tabs})
       free_buf(*b);
     if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
     for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
@@ -1149,9 +1149,10 @@ int fpw_periodogram_drift(fpw_ctx* ctx, void* stream, const fpw_params* params, 
     if (k > 0) FPW_CK(launch_fill_topk(topk_idx, topk_S, ncurves * k, st));
     return FPW_OK;
   }
-  FPW_CK(ensure(ctx->dr_payload, sizeof(float) * (size_t)drift_payload_floats() * (size_t)std::max<int64_t>(nobs, 1)));
+  FPW_CK(ensure(ctx->dr_payload, drift_payload_bytes() * (size_t)std::max<int64_t>(nobs, 1)));
   FPW_CK(ensure(ctx->dr_H0, sizeof(double) * 16 * (size_t)ncurves));
   FPW_CK(ensure(ctx->dr_g, sizeof(double) * 4 * (size_t)ncurves));
+  FPW_CK(ensure(ctx->dr_tabs, sizeof(double) * (size_t)ncurves));
   FPW_CK(ensure(ctx->curve_bad, (size_t)ncurves + 16));
   if (k > 0) FPW_CK(ensure(ctx->sh_S32, (size_t)ncurves * (size_t)nfreq * sizeof(float)));
   DriftArgs a{};
@@ -1166,7 +1167,8 @@ int fpw_periodogram_drift(fpw_ctx* ctx, void* stream, const fpw_params* params, 
   a.K = K;
   a.beta = beta;
   a.inv_alpha2 = p.inv_alpha2;
-  a.payload = static_cast<float*>(ctx->dr_payload.p);
+  a.payload = ctx->dr_payload.p;
+  a.tabs = static_cast<double*>(ctx->dr_tabs.p);
   a.H0 = static_cast<double*>(ctx->dr_H0.p);
   a.g = static_cast<double*>(ctx->dr_g.p);
   a.curve_bad = static_cast<uint8_t*>(ctx->curve_bad.p);

@@ -65,7 +65,8 @@ struct DriftArgs {
   int K;                    // Chebyshev basis functions (0..4)
   double beta;              // prior standard deviation of each basis coefficient
   double inv_alpha2;
-  float* payload;           // [nobs][6]: w x, w, w B_0..B_3
+  void* payload;            // [nobs] 32-byte per-observation records (prep kernel)
+  double* tabs;             // [ncurves] max |t| of the curve's finite times
   double* H0;               // [ncurves][4][4]: I + B^T D B
   double* g;                // [ncurves][4]: H0^-1 B^T D x
   uint8_t* curve_bad;       // [ncurves]
@@ -82,7 +83,7 @@ struct DriftArgs {
 int drift_threads(int M, int K, int smem_optin);  // threads per block, 0 if M is too large
 size_t drift_smem_bytes(int M, int K, int T);
 int drift_max_basis();
-int drift_payload_floats();
+size_t drift_payload_bytes();
 cudaError_t drift_init_attributes(int max_smem);
 cudaError_t launch_drift(const DriftArgs& a, int T, cudaStream_t st);
 
