@@ -49,6 +49,15 @@ __host__ __device__ constexpr int drift_stage_bytes(int K) { return 16 + 16 + (K
 // float4 for K = 2, 3, and Q_3 in a float of its own for K = 4.
 __host__ __device__ constexpr int drift_bin_bytes(int K) { return K <= 1 ? 8 : (K <= 3 ? 16 : 20); }
 
+// 1/L in binary64 from the FP32 reciprocal and one Newton-Raphson step
+// (r <- r + r (1 - L r)), which squares the FP32 estimate's relative error to
+// ~2^-46; an exact division where L lies outside [2^-100, 2^100].
+__device__ __forceinline__ double recip(double L) {
+  if (!(L > 0x1p-100 && L < 0x1p100)) return 1.0 / L;
+  const double r0 = (double)__frcp_rn((float)L);
+  return fma(r0, fma(-L, r0, 1.0), r0);
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -332,7 +341,7 @@ __global__ void __launch_bounds__(128) drift_kernel(const DriftArgs a) {
     const double L = Bw + cal;
     if (!(L > 0.0)) continue;  // empty bin with 1/alpha^2 = 0: dropped
     if (K > 0) Q[0] = beta * Bw;
-    const double rL = 1.0 / L;
+    const double rL = recip(L);
     double z = Y;
 #pragma unroll
     for (int p = 0; p < K; ++p) z -= Q[p] * g[p];
@@ -346,8 +355,9 @@ __global__ void __launch_bounds__(128) drift_kernel(const DriftArgs a) {
       for (int q = 0; q <= p; ++q) H[p][q] -= qs * Q[q];
     }
   }
-  // v^T H^-1 v by Cholesky (H >= I)
-  double Lc[kDrMaxK][kDrMaxK], y[kDrMaxK];
+  // v^T H^-1 v by Cholesky (H >= I): off-diagonal factors and the forward
+  // substitution multiply by the reciprocal square roots of the pivots
+  double Lc[kDrMaxK][kDrMaxK], di[kDrMaxK], y[kDrMaxK];
 #pragma unroll
   for (int p = 0; p < K; ++p)
 #pragma unroll
@@ -355,14 +365,17 @@ __global__ void __launch_bounds__(128) drift_kernel(const DriftArgs a) {
       double s = H[p][q];
 #pragma unroll
       for (int r = 0; r < q; ++r) s -= Lc[p][r] * Lc[q][r];
-      Lc[p][q] = (p == q) ? sqrt(s > 0.0 ? s : 0.0) : s / Lc[q][q];
+      if (p == q)
+        di[p] = s > 0.0 ? rsqrt(s) : 0.0;
+      else
+        Lc[p][q] = s * di[q];
     }
 #pragma unroll
   for (int p = 0; p < K; ++p) {
     double s = v[p];
 #pragma unroll
     for (int r = 0; r < p; ++r) s -= Lc[p][r] * y[r];
-    y[p] = Lc[p][p] > 0.0 ? s / Lc[p][p] : 0.0;
+    y[p] = s * di[p];
     S += y[p] * y[p];
   }
   const float Sf = cbad ? __int_as_float(0x7fc00000) : (float)S;
