@@ -124,3 +124,30 @@ def test_drift_ragged_10k_full_size_sampled(G, ctx):
             # a local maximum of the oracle's periodogram up to the FP32 tolerance
             assert np.all(Sc >= So - (2e-4 * np.abs(So) + 2e-7 * bound)), (c, fi, So)
         assert np.all(np.diff(Sk[c]) <= 1e-4 * np.abs(Sk[c][:-1]) + 1e-7 * bound)  # ranked by S
+
+
+def test_drift_zero_prior_width_is_eq1(G, ctx):
+    """beta = 0 removes the baseline (C_B = 0): with K = 3 the statistic is Eq. 1,
+    as the batched path computes it."""
+    w = L.ragged(312, [350, 90, 600], 1500, M=20, k=5)
+    _, _, Sd, st = run_drift(G, ctx, w, 20, 3, 0.0, 0)
+    assert st == 0
+    _, _, Sb, st = run_batch(ctx, w, k=0, dense=True)
+    assert st == 0
+    for c in range(w.ncurves):
+        t, x, s = w.curve(c)
+        assert_S_close(Sd[c], Sb[c], s_bound(x, s), rel=2e-4, what=f"beta=0 curve {c}")
+
+
+@pytest.mark.parametrize("ia2", [2.0 ** 110, 1e-35])
+def test_drift_extreme_inv_alpha2(G, ctx, ia2):
+    """1/alpha^2 far outside the range where a bin's 1/L comes from the FP32
+    reciprocal (above 2^100), and tiny: S against the dense oracle."""
+    w = L.ragged(313, [120, 260], 300, M=10, k=3)
+    _, _, Sd, st = run_drift(G, ctx, w, 10, 3, 1.0, 0, params=G.fpw_params_default(inv_alpha2=ia2))
+    assert st == 0
+    for c in range(w.ncurves):
+        t, x, s = w.curve(c)
+        S_or = oracle.fpw_drift(t, x, s, w.freqs, 10, 3, 1.0, ia2)
+        near = oracle.min_edge(t, w.freqs, 10) <= 1e-9
+        assert_S_close(Sd[c], S_or, s_bound(x, s), mask=~near, what=f"ia2={ia2:g} curve {c}")
