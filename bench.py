@@ -493,11 +493,38 @@ def run_gb300(args):
 
 
 # ---------------------------------------------------------------- per-workload report
+def timed_batch(ctx, w, M, k, params, reps=3):
+    """Evaluations/s of the batched call (whole call and tile kernel) and its ms."""
+    import torch
+
+    import paper_2502_00243_gb300 as G
+    d = [torch.from_numpy(a).cuda() for a in (w.offsets, w.t, w.x, w.sigma, w.freqs)]
+    C = w.ncurves
+    idx = torch.empty(max(C * k, 1), dtype=torch.int32, device="cuda")
+    S = torch.empty(max(C * k, 1), dtype=torch.float32, device="cuda")
+    call = lambda: G.fpw_periodogram_batch_ex(ctx, None, params, d[0], w.offsets, d[1], d[2], d[3], d[4], M, k,
+                                              idx if k else None, S if k else None)
+    call()
+    torch.cuda.synchronize()
+    ctx.set_timing(True)
+    ctx.kernel_time()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        call()
+    e1.record()
+    torch.cuda.synchronize()
+    kms, n = ctx.kernel_time()
+    ctx.set_timing(False)
+    ev = float(w.offsets[-1]) * w.nfreq
+    kern = ev / (kms / n / 1e3) if n > 0 and kms > 0 else None
+    return ev / (e0.elapsed_time(e1) / reps / 1e3), kern, e0.elapsed_time(e1) / reps
+
+
 def run_configs(args):
     """One JSON line per workload: device-resident evaluations/s of the batched
     fixed64 path (tile-kernel time and whole-call time), and the plain binary64
     form where it is cheap enough to time."""
-    import numpy as np
     import torch
 
     import lightcurves as L
@@ -507,33 +534,15 @@ def run_configs(args):
     nsm = torch.cuda.get_device_properties(0).multi_processor_count
     peak = nsm * sm_max_mhz() * 1e6 * SMEM_EVALS_PER_CLK_SM
 
-    def timed(w, M, k, params, reps=3):
-        d = [torch.from_numpy(a).cuda() for a in (w.offsets, w.t, w.x, w.sigma, w.freqs)]
-        C = w.ncurves
-        idx = torch.empty(max(C * k, 1), dtype=torch.int32, device="cuda")
-        S = torch.empty(max(C * k, 1), dtype=torch.float32, device="cuda")
-        call = lambda: G.fpw_periodogram_batch_ex(ctx, None, params, d[0], w.offsets, d[1], d[2], d[3], d[4], M, k,
-                                                  idx if k else None, S if k else None)
-        call()
-        torch.cuda.synchronize()
-        ctx.set_timing(True)
-        ctx.kernel_time()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(reps):
-            call()
-        e1.record()
-        torch.cuda.synchronize()
-        kms, n = ctx.kernel_time()
-        ctx.set_timing(False)
-        ev = float(w.offsets[-1]) * w.nfreq
-        kern = ev / (kms / n / 1e3) if n > 0 and kms > 0 else None
-        return ev / (e0.elapsed_time(e1) / reps / 1e3), kern, e0.elapsed_time(e1) / reps
+    timed = lambda w, M, k, params, reps=3: timed_batch(ctx, w, M, k, params, reps)
 
-    cases = [("single_plain", L.make("single_plain"), 10), ("single_ztf", L.make("single_ztf"), 20),
-             ("ragged_10k", L.make("ragged_10k"), 20), ("precision", L.make("precision", range(20)), 20)]
-    for M in (10, 20, 50):
-        cases.append((f"sweep_100k/M={M} (batch of 1e4 curves)", L.make("sweep_100k", range(10_000), M=M), M))
+    want = lambda sec: args.configs in ("all", sec)
+    cases = []
+    if want("batch"):
+        cases = [("single_plain", L.make("single_plain"), 10), ("single_ztf", L.make("single_ztf"), 20),
+                 ("ragged_10k", L.make("ragged_10k"), 20), ("precision", L.make("precision", range(20)), 20)]
+        for M in (10, 20, 50):
+            cases.append((f"sweep_100k/M={M} (batch of 1e4 curves)", L.make("sweep_100k", range(10_000), M=M), M))
     for name, w, M in cases:
         call_rate, kern_rate, ms = timed(w, M, w.k, G.fpw_params_default())
         line = {"config": name, "curves": w.ncurves, "nobs": int(w.offsets[-1]), "nfreq": w.nfreq, "M": M,
@@ -548,7 +557,26 @@ def run_configs(args):
             line["graph_evals_per_s_call"] = gr
         print(json.dumps(line), flush=True)
 
-    # curves sharing their times: the tensor-core path against the batched path on the same curves
+    if want("shared"):
+        run_configs_shared(ctx, peak)
+    if want("drift"):
+        run_configs_drift(ctx, peak)
+    if want("multi"):
+        run_configs_multi(ctx, peak)
+    if want("entropy"):
+        run_configs_entropy(ctx, peak)
+    ctx.close()
+    return 0
+
+
+def run_configs_shared(ctx, peak):
+    """Curves sharing their times: the tensor-core path against the batched path
+    on the same curves."""
+    import numpy as np
+    import torch
+
+    import lightcurves as L
+    import paper_2502_00243_gb300 as G
     w = L.make("shared_4096")
     C, n = w.ncurves, L.SHARED_N
     d = [torch.from_numpy(np.ascontiguousarray(a)).cuda()
@@ -575,7 +603,7 @@ def run_configs(args):
     npass = -(-w.nfreq // (2 * fpm))
     flops = 2.0 * 128 * 2 * n_mma * (-(-n // 32) * 64) * npass * (-(-C // 64))  # issued MMA flops per call
     kern_s = kms / nl / 1e3
-    tile_rate, tile_kern, _ = timed(w, w.M, w.k, G.fpw_params_default())
+    tile_rate, tile_kern, _ = timed_batch(ctx, w, w.M, w.k, G.fpw_params_default())
     line = {"config": "shared_4096 (4096 curves sharing N=1000 times, M=20, 5e5 freqs, top-5)", "curves": C,
             "nobs_shared": n, "nfreq": w.nfreq, "M": w.M, "evals": ev,
             "ms_per_call": e0.elapsed_time(e1) / reps, "evals_per_s_call": ev / (e0.elapsed_time(e1) / reps / 1e3),
@@ -586,7 +614,14 @@ def run_configs(args):
             "batched_path_same_curves_evals_per_s_tile_kernel": tile_kern}
     print(json.dumps(line), flush=True)
 
-    # baseline drift marginalised (K = 3 Chebyshev terms, beta = 1) on the ragged batch
+
+def run_configs_drift(ctx, peak):
+    """Baseline drift marginalised (K = 3 Chebyshev terms, beta = 1) on the
+    ragged batch."""
+    import torch
+
+    import lightcurves as L
+    import paper_2502_00243_gb300 as G
     w = L.make("ragged_10k")
     d = [torch.from_numpy(a).cuda() for a in (w.offsets, w.t, w.x, w.sigma, w.freqs)]
     idx = torch.empty(w.ncurves * w.k, dtype=torch.int32, device="cuda")
@@ -610,8 +645,93 @@ def run_configs(args):
                       "smem_roof_evals_per_s": peak * 16.0 / 32.0,
                       "roofline_frac": ev / (kms / nl / 1e3) / (peak * 16.0 / 32.0),
                       "note": "K=3: one (Y, Bw, Q_1, Q_2) float4 read-modify-write (2 x 16 B) per evaluation"}), flush=True)
-    ctx.close()
-    return 0
+
+
+def run_configs_multi(ctx, peak):
+    """Several M from one M_max pass (Section 3.4) on one 1e4-curve batch of the
+    sweep: M_max = 20 (M = 20, 10, 5), 40 and 60 (M = 20, 10, 4, with 2..15
+    bin offsets each), against the single-M call at M = 20 on the same batch.
+    An evaluation is one (observation, frequency) pair accumulated at M_max."""
+    import torch
+
+    import lightcurves as L
+    import paper_2502_00243_gb300 as G
+    w = L.make("sweep_100k", range(10_000), M=20)
+    d = [torch.from_numpy(a).cuda() for a in (w.offsets, w.t, w.x, w.sigma, w.freqs)]
+    ev = float(w.offsets[-1]) * w.nfreq
+    for M_max, groups in ((20, (1, 2, 4)), (40, (2, 4, 10)), (60, (3, 6, 15))):
+        ng, k = len(groups), w.k
+        idx = torch.empty(w.ncurves * ng * k, dtype=torch.int32, device="cuda")
+        off = torch.empty(w.ncurves * ng * k, dtype=torch.int32, device="cuda")
+        Sk = torch.empty(w.ncurves * ng * k, dtype=torch.float32, device="cuda")
+        call = lambda: G.fpw_periodogram_batch_multi(ctx, None, None, d[0], w.offsets, d[1], d[2], d[3], d[4],
+                                                     M_max, groups, k, idx, off, Sk)
+        call()
+        torch.cuda.synchronize()
+        ctx.set_timing(True)
+        ctx.kernel_time()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        call()
+        e1.record()
+        torch.cuda.synchronize()
+        kms, nl = ctx.kernel_time()
+        ctx.set_timing(False)
+        kern = ev / (kms / nl / 1e3)
+        print(json.dumps({"config": f"sweep_100k batch of 1e4 curves, several M: M_max={M_max}, "
+                                    f"M={[M_max // g for g in groups]} with every offset, top-{k} per M",
+                          "evals": ev, "ms_per_call": e0.elapsed_time(e1),
+                          "evals_per_s_call": ev / (e0.elapsed_time(e1) / 1e3), "evals_per_s_tile_kernel": kern,
+                          "roofline_frac": kern / peak, "status": ctx.status(),
+                          "note": "roof: the 16 B (A, B) read-modify-write per evaluation at M_max bins"}), flush=True)
+
+
+def run_configs_entropy(ctx, peak):
+    """Phase entropy (Appendix C): the dense H(f) of the N = 1000 ZTF-cadence
+    times over 1e6 frequencies, and H with its z-score at the top-5 peaks of
+    the 1e4 ragged curves."""
+    import torch
+
+    import lightcurves as L
+    import paper_2502_00243_gb300 as G
+    w = L.make("single_ztf")
+    t, fr = torch.from_numpy(w.t).cuda(), torch.from_numpy(w.freqs).cuda()
+    H = torch.empty(w.nfreq, dtype=torch.float32, device="cuda")
+    for M in (20, 50):
+        G.fpw_phase_entropy(ctx, None, t, fr, M, H)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        G.fpw_phase_entropy(ctx, None, t, fr, M, H)
+        e1.record()
+        torch.cuda.synchronize()
+        ev = float(w.t.size) * w.nfreq
+        rate = ev / (e0.elapsed_time(e1) / 1e3)
+        print(json.dumps({"config": f"single_ztf times (N={w.t.size}), dense phase entropy, M={M}, "
+                                    f"{w.nfreq:.0e} freqs 0.01-100 1/d", "evals": ev,
+                          "ms_per_call": e0.elapsed_time(e1), "evals_per_s_call": rate,
+                          "roofline_frac": rate / (2.0 * peak), "status": ctx.status(),
+                          "note": "roof: a 4 B count read-modify-write (8 B) per evaluation, 16 evals/clk/SM"}),
+              flush=True)
+    r = L.make("ragged_10k")
+    d = [torch.from_numpy(a).cuda() for a in (r.offsets, r.t, r.x, r.sigma, r.freqs)]
+    k = r.k
+    idx = torch.empty(r.ncurves * k, dtype=torch.int32, device="cuda")
+    Sk = torch.empty(r.ncurves * k, dtype=torch.float32, device="cuda")
+    G.fpw_periodogram_batch_ex(ctx, None, None, d[0], r.offsets, d[1], d[2], d[3], d[4], r.M, k, idx, Sk)
+    Hp = torch.empty(r.ncurves * k, dtype=torch.float32, device="cuda")
+    zp = torch.empty(r.ncurves * k, dtype=torch.float32, device="cuda")
+    G.fpw_phase_entropy_peaks(ctx, None, d[0], d[1], d[4], r.M, k, idx, Hp, zp)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    G.fpw_phase_entropy_peaks(ctx, None, d[0], d[1], d[4], r.M, k, idx, Hp, zp)
+    e1.record()
+    torch.cuda.synchronize()
+    ev = float(r.offsets[-1]) * k
+    print(json.dumps({"config": f"ragged_10k top-{k} peaks: H and Hutcheson z per peak, M={r.M}", "evals": ev,
+                      "ms_per_call": e0.elapsed_time(e1), "evals_per_s_call": ev / (e0.elapsed_time(e1) / 1e3),
+                      "status": ctx.status()}), flush=True)
 
 
 def run_case(args):
@@ -678,7 +798,9 @@ def main(argv=None):
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--autotune", action="store_true", help="measure and install tuned kernel shapes before timing")
-    ap.add_argument("--configs", action="store_true", help="report every workload (one JSON line each) instead")
+    ap.add_argument("--configs", nargs="?", const="all", default=None,
+                    choices=["all", "batch", "shared", "drift", "multi", "entropy"],
+                    help="report every workload (one JSON line each) instead, or one section of them")
     ap.add_argument("--case", choices=["shared", "drift"], help="one small call of that path (profiling case)")
     ap.add_argument("--case-curves", type=int, default=256)
     args = ap.parse_args(argv)

@@ -6,9 +6,8 @@
 // used to flag periodogram peaks whose phase coverage is anomalously uneven
 // (z = (H - E) / sqrt(Var) strongly negative).
 //
-// Bins use the exact anchor of the periodogram kernels
-// (bin_of_phase(phase_fixed64(t, f))), so they agree with the tile kernels'
-// bins except within 2^-32 cycles of an edge.
+// Bins use the exact anchors and 64-bit stepping of the periodogram kernels,
+// so they equal floor(M frac(t f)) except within 2e-10 cycles of an edge.
 #include <math.h>
 
 #include "fpw_internal.cuh"
@@ -25,26 +24,60 @@ __device__ __forceinline__ float entropy_from_counts_sum(float sum_clogc, float 
   return N > 0.f ? logf(N) - sum_clogc / N : 0.f;
 }
 
-// One thread per frequency; observation times staged in shared memory; counts
-// per (bin, thread) as 32-bit integers, [m][thread] (conflict-free).
+// One thread per frequency, blocks of kEntThreads consecutive frequencies;
+// counts per (bin, thread) as 32-bit integers, [m][thread] (conflict-free).
+// Per staged observation the block holds the exact anchor phase at its first
+// frequency, P_i = frac(t_i f_0), and the step D_i = frac(t_i df) as 64-bit
+// fixed point; where the block's frequencies lie on the linear grid (the tile
+// kernels' bound on the phase error) thread j's phase is P_i + j D_i (mod
+// 2^64), as in the periodogram kernels, else the exact anchor at its own
+// frequency. Two observations per iteration, both counts loaded before either
+// store (a shared bin counts both).
 __global__ void __launch_bounds__(kEntThreads) entropy_dense_kernel(const double* t, int64_t n, const double* freqs,
                                                                     int64_t nfreq, int M, float* H_out) {
   extern __shared__ __align__(16) unsigned char smem[];
-  double* st = reinterpret_cast<double*>(smem);
-  unsigned* cnt = reinterpret_cast<unsigned*>(st + kEntChunk);
+  ulonglong2* const sPD = reinterpret_cast<ulonglong2*>(smem);
+  unsigned* const cnt = reinterpret_cast<unsigned*>(sPD + kEntChunk);
+  __shared__ double s_tm[kEntThreads / 32];
   const int tid = threadIdx.x;
-  const int64_t k = (int64_t)blockIdx.x * kEntThreads + tid;
-  const double f = freqs[k < nfreq ? k : nfreq - 1];
+  const int64_t f0 = (int64_t)blockIdx.x * kEntThreads, k = f0 + tid;
+  const double fa = freqs[f0];
+  const double fk = freqs[k < nfreq ? k : nfreq - 1];
+  const double df = (nfreq > 1) ? (freqs[nfreq - 1] - freqs[0]) / (double)(nfreq - 1) : 0.0;
+  double tm = 0.0;
+  for (int64_t i = tid; i < n; i += kEntThreads) tm = fmax(tm, fabs(t[i]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) tm = fmax(tm, __shfl_xor_sync(0xffffffffu, tm, o));
+  if ((tid & 31) == 0) s_tm[tid >> 5] = tm;
+  __syncthreads();
+  tm = 0.0;
+#pragma unroll
+  for (int q = 0; q < kEntThreads / 32; ++q) tm = fmax(tm, s_tm[q]);
+  const bool nonlin = k < nfreq && fabs(fk - fma((double)tid, df, fa)) * tm > kGridTolCycles;
+  const bool lin = !__syncthreads_or(nonlin);
   for (int m = 0; m < M; ++m) cnt[m * kEntThreads + tid] = 0u;
   for (int64_t o = 0; o < n; o += kEntChunk) {
     const int c = (int)((n - o) < kEntChunk ? (n - o) : kEntChunk);
     __syncthreads();
-    for (int i = tid; i < c; i += kEntThreads) st[i] = t[o + i];
-    __syncthreads();
-    for (int i = 0; i < c; ++i) {
-      const unsigned m = bin_of_phase(phase_fixed64(st[i], f), (unsigned)M);
-      cnt[m * kEntThreads + tid] += 1u;
+    for (int i = tid; i < c; i += kEntThreads) {
+      const double ti = t[o + i];
+      sPD[i] = lin ? make_ulonglong2(phase_fixed64(ti, fa), phase_fixed64(ti, df))
+                   : make_ulonglong2((unsigned long long)__double_as_longlong(ti), 0ull);
     }
+    __syncthreads();
+    auto slot = [&](const ulonglong2 pd) {
+      const unsigned long long phi =
+          lin ? pd.x + (unsigned long long)tid * pd.y : phase_fixed64(__longlong_as_double((long long)pd.x), fk);
+      return (int)bin_of_phase(phi, (unsigned)M) * kEntThreads + tid;
+    };
+    int i = 0;
+    for (; i + 1 < c; i += 2) {
+      const int ma = slot(sPD[i]), mb = slot(sPD[i + 1]);
+      const unsigned va = cnt[ma], vb = cnt[mb];
+      cnt[ma] = va + 1u;
+      cnt[mb] = (ma == mb ? va + 1u : vb) + 1u;
+    }
+    if (i < c) cnt[slot(sPD[i])] += 1u;
   }
   if (k < nfreq) {
     float s = 0.f;
@@ -113,7 +146,7 @@ __global__ void __launch_bounds__(kPeakWarps * 32) entropy_peaks_kernel(const in
 cudaError_t launch_entropy_dense(const double* t, int64_t n, const double* freqs, int64_t nfreq, int M, float* H_out,
                                  cudaStream_t st) {
   if (nfreq <= 0) return cudaSuccess;
-  const size_t smem = (size_t)kEntChunk * 8 + (size_t)M * kEntThreads * 4;
+  const size_t smem = (size_t)kEntChunk * 16 + (size_t)M * kEntThreads * 4;
   cudaError_t e = cudaFuncSetAttribute(entropy_dense_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int64_t blocks = (nfreq + kEntThreads - 1) / kEntThreads;

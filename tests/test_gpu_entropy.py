@@ -40,6 +40,28 @@ def test_dense_phase_entropy(G, M):
     ctx.close()
 
 
+@pytest.mark.parametrize("M", [1, 7, 256])
+def test_dense_phase_entropy_irregular_grid(G, M):
+    """A grid that is not linear (every frequency anchored exactly), M from 1 to
+    256, a frequency count that leaves a partial block, and no observations."""
+    rng = np.random.default_rng([91, M])
+    t = np.sort(rng.uniform(0.0, 900.0, 700))
+    freqs = np.sort(rng.uniform(0.01, 40.0, 3001))
+    ctx = G.Context(0)
+    H = torch.empty(freqs.size, dtype=torch.float32, device="cuda")
+    G.fpw_phase_entropy(ctx, None, torch.from_numpy(t).cuda(), torch.from_numpy(freqs).cuda(), M, H)
+    torch.cuda.synchronize()
+    Hn = H.cpu().numpy().astype(np.float64)
+    H_or = oracle.phase_entropy(t, freqs, M)
+    near = oracle.min_edge(t, freqs, M) <= 1e-9
+    err = np.abs(Hn - H_or)[~near]
+    assert err.max() < 2e-5, err.max()
+    G.fpw_phase_entropy(ctx, None, torch.from_numpy(t[:0].copy()).cuda(), torch.from_numpy(freqs).cuda(), M, H)
+    torch.cuda.synchronize()
+    assert torch.all(H == 0.0)
+    ctx.close()
+
+
 def test_entropy_at_batch_peaks(G):
     w = L.ragged(80, [300, 1500, 60, 900], 6000, M=20, k=5)
     ctx = G.Context(0)
