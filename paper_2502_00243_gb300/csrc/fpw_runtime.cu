@@ -187,9 +187,12 @@ int choose_shape(fpw_ctx* ctx, const fpw_params& p, int M, int k, int64_t max_n,
     R = 8;
   else if (M <= 24)
     R = n_typ < 300 ? 2 : 4;
-  else if (M <= 64)
+  else if (M <= 50)
     R = 2;
-  else
+  else if (M <= 64) {  // two blocks of 6 warps per SM (T = 128, R = 2 leaves one block of 4)
+    T = 192;
+    R = 1;
+  } else
     R = 1;
   for (const ShapeEntry& e : ctx->shapes)
     if (M >= e.M_lo && M <= e.M_hi && n_typ >= e.n_lo && n_typ < e.n_hi) {

@@ -91,6 +91,7 @@ RAGGED = [
     ([1500, 10, 800], 2500, 20, 5, {"accum": 1}),
     ([1500, 10, 800], 2500, 20, 5, {"peak_mode": 1}),
     ([600, 2100], 1999, 64, 7, {"inv_alpha2": 0.5}),
+    ([50, 1700, 333], 2111, 55, 5, {}),
 ]
 
 
