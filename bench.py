@@ -735,9 +735,10 @@ def run_configs_entropy(ctx, peak):
 
 
 def run_case(args):
-    """One small call of the shared-timestamp or the baseline-drift path, for
-    profiling: two untimed calls, then one call timed with the library's
-    kernel-timing hook; prints one JSON line."""
+    """One small call of the shared-timestamp, baseline-drift, several-M or
+    phase-entropy path, for profiling: two untimed calls, then one call timed
+    with the library's kernel-timing hook (CUDA events around the call for the
+    entropy kernel, the call's only launch); prints one JSON line."""
     import numpy as np
     import torch
 
@@ -757,12 +758,44 @@ def run_case(args):
         call = lambda: G.fpw_periodogram_shared(ctx, None, None, d[0], d[1], d[2], d[3], 20, 5, idx, Sk)
         ev = float(C) * n * F
         what = f"shared_4096: {C} curves sharing N={n} times, M=20, {F} freqs 0.01-50 1/d, top-5"
-    else:
+    elif args.case == "drift":
         w = L.make("ragged_10k", range(C), nfreq=F)
         d = [torch.from_numpy(a).cuda() for a in (w.offsets, w.t, w.x, w.sigma, w.freqs)]
         call = lambda: G.fpw_periodogram_drift(ctx, None, None, d[0], d[1], d[2], d[3], d[4], 20, 3, 1.0, 5, idx, Sk)
         ev = float(w.offsets[-1]) * F
         what = f"ragged_10k: first {C} curves, baseline drift K=3 beta=1, M=20, {F} freqs 0.02-50 1/d, top-5"
+    elif args.case == "multi":
+        w = L.make("sweep_100k", range(C), M=20, nfreq=F)
+        d = [torch.from_numpy(a).cuda() for a in (w.offsets, w.t, w.x, w.sigma, w.freqs)]
+        groups = (3, 6, 15)
+        mi = torch.empty(C * 5 * len(groups), dtype=torch.int32, device="cuda")
+        mo = torch.empty_like(mi)
+        ms = torch.empty(C * 5 * len(groups), dtype=torch.float32, device="cuda")
+        call = lambda: G.fpw_periodogram_batch_multi(ctx, None, None, d[0], w.offsets, d[1], d[2], d[3], d[4], 60,
+                                                     groups, 5, mi, mo, ms)
+        ev = float(w.offsets[-1]) * F
+        what = f"sweep_100k: first {C} curves, several M from M_max=60 (M=20, 10, 4), {F} freqs 0.01-50 1/d, top-5"
+    else:
+        w = L.make("single_ztf", nfreq=F)
+        t, fr = torch.from_numpy(w.t).cuda(), torch.from_numpy(w.freqs).cuda()
+        H = torch.empty(F, dtype=torch.float32, device="cuda")
+        call = lambda: G.fpw_phase_entropy(ctx, None, t, fr, 20, H)
+        ev = float(w.t.size) * F
+        what = f"single_ztf times (N={w.t.size}), dense phase entropy, M=20, {F} freqs 0.01-100 1/d"
+        call()
+        call()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        call()
+        e1.record()
+        torch.cuda.synchronize()
+        ms_ = e0.elapsed_time(e1)
+        st = ctx.status()
+        print(json.dumps({"case": args.case, "config": what, "status": st, "call_ms": ms_, "evals": ev,
+                          "evals_per_s_call": ev / (ms_ / 1e3)}), flush=True)
+        ctx.close()
+        return 0 if st == 0 else 1
     call()
     call()
     torch.cuda.synchronize()
@@ -801,7 +834,8 @@ def main(argv=None):
     ap.add_argument("--configs", nargs="?", const="all", default=None,
                     choices=["all", "batch", "shared", "drift", "multi", "entropy"],
                     help="report every workload (one JSON line each) instead, or one section of them")
-    ap.add_argument("--case", choices=["shared", "drift"], help="one small call of that path (profiling case)")
+    ap.add_argument("--case", choices=["shared", "drift", "multi", "entropy"],
+                    help="one small call of that path (profiling case)")
     ap.add_argument("--case-curves", type=int, default=256)
     args = ap.parse_args(argv)
     if args.warmup < 0 or args.steps < 1:
