@@ -463,9 +463,17 @@ def run_gb300(args):
         b0 = ids[0]
         pick, F_s = oracle_sample(host[b0], F_grid, args.M, k, args.cpu_seconds, cores)
         ev, dt = oracle_rate(host[b0], pick, F_s, args.M, k, cores)
+        # one core: the sample's median-N curve over the first 2e5 grid frequencies (about 1 s)
+        o_b = host[b0][0]
+        n_pick = o_b[np.asarray(pick) + 1] - o_b[np.asarray(pick)]
+        one = [int(np.asarray(pick)[np.argsort(n_pick, kind="stable")[len(pick) // 2]])]
+        ev1, dt1 = oracle_rate(host[b0], one, F_s[:200_000], args.M, k, 1)
         cpu = {"value": ev / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{len(pick)} curves stratified by N from batch {b0} x {F_s.shape[0]} of the {F} grid "
-                         f"frequencies, M={args.M}, top-{k}, {cores} threads ({ev:.3g} evals in {dt:.1f} s)"}
+                         f"frequencies, M={args.M}, top-{k}, {cores} threads ({ev:.3g} evals in {dt:.1f} s)",
+               "single_core_value": ev1 / dt1,
+               "single_core_sample": f"curve {one[0]} of batch {b0} (the sample's median N) x the first "
+                                     f"{min(200_000, F_s.shape[0])} of those frequencies, one thread"}
 
     if rank == 0:
         nsm = torch.cuda.get_device_properties(local_rank).multi_processor_count
