@@ -151,3 +151,21 @@ def test_drift_extreme_inv_alpha2(G, ctx, ia2):
         S_or = oracle.fpw_drift(t, x, s, w.freqs, 10, 3, 1.0, ia2)
         near = oracle.min_edge(t, w.freqs, 10) <= 1e-9
         assert_S_close(Sd[c], S_or, s_bound(x, s), mask=~near, what=f"ia2={ia2:g} curve {c}")
+
+
+def test_drift_irregular_grid(G, ctx):
+    """A grid that is not linear: every (observation, frequency) pair takes its
+    exact anchor; a linear head and an irregular tail in one call."""
+    w = L.ragged(314, [300, 45, 800], 700, M=16, k=4)
+    rng = np.random.default_rng(5)
+    w.freqs = np.concatenate([np.linspace(0.02, 5.0, 300), np.sort(rng.uniform(5.01, 35.0, 400))])
+    idx, Sk, Sd, st = run_drift(G, ctx, w, 16, 3, 1.5, 4)
+    assert st == 0
+    for c in range(w.ncurves):
+        t, x, s = w.curve(c)
+        S_or = oracle.fpw_drift(t, x, s, w.freqs, 16, 3, 1.5)
+        bound = s_bound(x, s)
+        near = oracle.min_edge(t, w.freqs, 16) <= 1e-9
+        assert_S_close(Sd[c], S_or, bound, mask=~near, what=f"irregular grid curve {c}")
+        o_idx, o_S = oracle.topk(S_or, 8)
+        check_topk(idx[c], Sk[c], o_idx, o_S, abs_tol=1e-7 * bound, o_dense=S_or, what=f"irregular grid curve {c}")

@@ -143,3 +143,20 @@ def test_shared_4096_full_size_sampled(G, ctx):
         assert_S_close(sub_dense[j], S_or, bound, mask=~near, what=f"shared_4096 curve {c}")
         o_idx, o_S = oracle.topk(S_or, w.k + 4)
         check_topk(idx[c], Sk[c], o_idx, o_S, abs_tol=1e-7 * bound, o_dense=S_or, what=f"shared_4096 curve {c}")
+
+
+def test_shared_irregular_grid(G, ctx):
+    """A grid that is not linear: the one-hot rows come from exact anchors per
+    (observation, frequency) pair, across several frequency passes."""
+    t, x, sigma, _ = field(5, 70, 300, 10)
+    rng = np.random.default_rng(8)
+    freqs = np.concatenate([np.linspace(0.05, 3.0, 100), np.sort(rng.uniform(3.01, 45.0, 700))])
+    idx, Sk, Sd, st = run_shared(G, ctx, t, x, sigma, freqs, 20, 5)
+    assert st == 0
+    S_or = oracle.fpw_shared(t, x, sigma, freqs, 20)
+    near = oracle.min_edge(t, freqs, 20) <= 1e-9
+    for c in range(70):
+        bound = s_bound(x[c], sigma[c])
+        assert_S_close(Sd[c], S_or[c], bound, mask=~near, what=f"irregular grid curve {c}")
+        o_idx, o_S = oracle.topk(S_or[c], 9)
+        check_topk(idx[c], Sk[c], o_idx, o_S, abs_tol=1e-7 * bound, o_dense=S_or[c], what=f"irregular grid curve {c}")
