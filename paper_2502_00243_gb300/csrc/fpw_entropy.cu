@@ -24,15 +24,16 @@ __device__ __forceinline__ float entropy_from_counts_sum(float sum_clogc, float 
   return N > 0.f ? logf(N) - sum_clogc / N : 0.f;
 }
 
-// One thread per frequency, blocks of kEntThreads consecutive frequencies;
-// counts per (bin, thread) as 32-bit integers, [m][thread] (conflict-free).
-// Per staged observation the block holds the exact anchor phase at its first
-// frequency, P_i = frac(t_i f_0), and the step D_i = frac(t_i df) as 64-bit
-// fixed point; where the block's frequencies lie on the linear grid (the tile
-// kernels' bound on the phase error) thread j's phase is P_i + j D_i (mod
-// 2^64), as in the periodogram kernels, else the exact anchor at its own
-// frequency. Two observations per iteration, both counts loaded before either
-// store (a shared bin counts both).
+// R consecutive frequencies per thread, blocks of kEntThreads R frequencies;
+// counts per (frequency slot, bin, thread) as 32-bit integers, [r][m][thread]
+// (conflict-free). Per staged observation the block holds the exact anchor
+// phase at its first frequency, P_i = frac(t_i f_0), and the step D_i =
+// frac(t_i df) as 64-bit fixed point; where the block's frequencies lie on the
+// linear grid (the tile kernels' bound on the phase error) frequency j of the
+// block has phase P_i + j D_i (mod 2^64), as in the periodogram kernels, else
+// the exact anchor at its own frequency. Two observations per iteration, all
+// counts loaded before any store (a shared bin counts both).
+template <int R>
 __global__ void __launch_bounds__(kEntThreads) entropy_dense_kernel(const double* t, int64_t n, const double* freqs,
                                                                     int64_t nfreq, int M, float* H_out) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -40,10 +41,16 @@ __global__ void __launch_bounds__(kEntThreads) entropy_dense_kernel(const double
   unsigned* const cnt = reinterpret_cast<unsigned*>(sPD + kEntChunk);
   __shared__ double s_tm[kEntThreads / 32];
   const int tid = threadIdx.x;
-  const int64_t f0 = (int64_t)blockIdx.x * kEntThreads, k = f0 + tid;
+  const int64_t f0 = (int64_t)blockIdx.x * (kEntThreads * R);
+  const int j0 = tid * R;  // the thread's first frequency within the block
   const double fa = freqs[f0];
-  const double fk = freqs[k < nfreq ? k : nfreq - 1];
   const double df = (nfreq > 1) ? (freqs[nfreq - 1] - freqs[0]) / (double)(nfreq - 1) : 0.0;
+  double fk[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int64_t k = f0 + j0 + r;
+    fk[r] = freqs[k < nfreq ? k : nfreq - 1];
+  }
   double tm = 0.0;
   for (int64_t i = tid; i < n; i += kEntThreads) tm = fmax(tm, fabs(t[i]));
 #pragma unroll
@@ -53,9 +60,13 @@ __global__ void __launch_bounds__(kEntThreads) entropy_dense_kernel(const double
   tm = 0.0;
 #pragma unroll
   for (int q = 0; q < kEntThreads / 32; ++q) tm = fmax(tm, s_tm[q]);
-  const bool nonlin = k < nfreq && fabs(fk - fma((double)tid, df, fa)) * tm > kGridTolCycles;
+  bool nonlin = false;
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+    if (f0 + j0 + r < nfreq && fabs(fk[r] - fma((double)(j0 + r), df, fa)) * tm > kGridTolCycles) nonlin = true;
   const bool lin = !__syncthreads_or(nonlin);
-  for (int m = 0; m < M; ++m) cnt[m * kEntThreads + tid] = 0u;
+  const int MT = M * kEntThreads;
+  for (int q = 0; q < R * M; ++q) cnt[q * kEntThreads + tid] = 0u;
   for (int64_t o = 0; o < n; o += kEntChunk) {
     const int c = (int)((n - o) < kEntChunk ? (n - o) : kEntChunk);
     __syncthreads();
@@ -65,27 +76,57 @@ __global__ void __launch_bounds__(kEntThreads) entropy_dense_kernel(const double
                    : make_ulonglong2((unsigned long long)__double_as_longlong(ti), 0ull);
     }
     __syncthreads();
-    auto slot = [&](const ulonglong2 pd) {
-      const unsigned long long phi =
-          lin ? pd.x + (unsigned long long)tid * pd.y : phase_fixed64(__longlong_as_double((long long)pd.x), fk);
-      return (int)bin_of_phase(phi, (unsigned)M) * kEntThreads + tid;
+    // count slots of one observation for the thread's R frequencies
+    auto slots = [&](const ulonglong2 pd, int (&sl)[R]) {
+      if (lin) {
+        unsigned long long phi = pd.x + (unsigned long long)j0 * pd.y;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          sl[r] = r * MT + (int)bin_of_phase(phi, (unsigned)M) * kEntThreads + tid;
+          phi += pd.y;
+        }
+      } else {
+        const double ti = __longlong_as_double((long long)pd.x);
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+          sl[r] = r * MT + (int)bin_of_phase(phase_fixed64(ti, fk[r]), (unsigned)M) * kEntThreads + tid;
+      }
     };
     int i = 0;
     for (; i + 1 < c; i += 2) {
-      const int ma = slot(sPD[i]), mb = slot(sPD[i + 1]);
-      const unsigned va = cnt[ma], vb = cnt[mb];
-      cnt[ma] = va + 1u;
-      cnt[mb] = (ma == mb ? va + 1u : vb) + 1u;
+      int sa[R], sb[R];
+      slots(sPD[i], sa);
+      slots(sPD[i + 1], sb);
+      unsigned va[R], vb[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        va[r] = cnt[sa[r]];
+        vb[r] = cnt[sb[r]];
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        cnt[sa[r]] = va[r] + 1u;
+        cnt[sb[r]] = (sa[r] == sb[r] ? va[r] + 1u : vb[r]) + 1u;
+      }
     }
-    if (i < c) cnt[slot(sPD[i])] += 1u;
+    if (i < c) {
+      int sa[R];
+      slots(sPD[i], sa);
+#pragma unroll
+      for (int r = 0; r < R; ++r) cnt[sa[r]] += 1u;
+    }
   }
-  if (k < nfreq) {
-    float s = 0.f;
-    for (int m = 0; m < M; ++m) {
-      const unsigned c = cnt[m * kEntThreads + tid];
-      if (c > 1u) s += (float)c * logf((float)c);
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int64_t k = f0 + j0 + r;
+    if (k < nfreq) {
+      float s = 0.f;
+      for (int m = 0; m < M; ++m) {
+        const unsigned q = cnt[r * MT + m * kEntThreads + tid];
+        if (q > 1u) s += (float)q * logf((float)q);
+      }
+      H_out[k] = entropy_from_counts_sum(s, (float)n);
     }
-    H_out[k] = entropy_from_counts_sum(s, (float)n);
   }
 }
 
@@ -146,12 +187,18 @@ __global__ void __launch_bounds__(kPeakWarps * 32) entropy_peaks_kernel(const in
 cudaError_t launch_entropy_dense(const double* t, int64_t n, const double* freqs, int64_t nfreq, int M, float* H_out,
                                  cudaStream_t st) {
   if (nfreq <= 0) return cudaSuccess;
-  const size_t smem = (size_t)kEntChunk * 16 + (size_t)M * kEntThreads * 4;
-  cudaError_t e = cudaFuncSetAttribute(entropy_dense_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // two frequencies per thread while the counts stay small (M <= 96: 96 KB per
+  // block at most), one beyond
+  const int R = M <= 96 ? 2 : 1;
+  const void* fn = R == 2 ? reinterpret_cast<const void*>(&entropy_dense_kernel<2>)
+                          : reinterpret_cast<const void*>(&entropy_dense_kernel<1>);
+  const size_t smem = (size_t)kEntChunk * 16 + (size_t)R * M * kEntThreads * 4;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const int64_t blocks = (nfreq + kEntThreads - 1) / kEntThreads;
-  entropy_dense_kernel<<<(unsigned)blocks, kEntThreads, smem, st>>>(t, n, freqs, nfreq, M, H_out);
-  return cudaGetLastError();
+  const int64_t per_block = (int64_t)kEntThreads * R;
+  const int64_t blocks = (nfreq + per_block - 1) / per_block;
+  void* args[] = {const_cast<double**>(&t), &n, const_cast<double**>(&freqs), &nfreq, &M, &H_out};
+  return cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(kEntThreads), args, smem, st);
 }
 
 cudaError_t launch_entropy_peaks(const int64_t* offsets, int64_t ncurves, const double* t, const double* freqs,
