@@ -18,7 +18,8 @@
 //
 // Bins with no observation and 1/alpha^2 = 0 are dropped (their rows vanish).
 // B_0 = beta T_0 = beta is constant, so Q_m0 = beta Bw_m needs no sum of its
-// own: a bin holds Y, Bw and Q_m1..Q_m(K-1), 1 + max(K, 1) floats.
+// own: a bin holds Y, Bw and Q_m1..Q_m(K-1), 1 + max(K, 1) floats; the row of
+// H and the entry of v that belong to B_0 take closed forms in the bin sums.
 // The sums accumulate in FP32 in thread-private shared-memory bins (one thread
 // per frequency, packed as float2 / float4 / float4 + float), phases are the
 // exact 64-bit anchors of the tile kernels stepped across a tile of
@@ -312,7 +313,14 @@ __global__ void __launch_bounds__(128) drift_kernel(const DriftArgs a) {
     }
   }
   if (k >= F) return;
-  // binary64 reduction: S = sum z^2 / L + v^T H^-1 v, H kept as its lower triangle
+  // binary64 reduction: S = sum z^2 / L + v^T H^-1 v, H kept as its lower
+  // triangle. The constant basis function B_0 = beta has Q_m0 = beta Bw_m, and
+  // sum_i w_i B_ip = sum_m Q_mp, so its row of H and its entry of v take
+  // closed forms in the bin sums,
+  //   H_00 = 1 + beta^2 (1/alpha^2) sum_m Bw_m / L_m,
+  //   H_p0 = beta (1/alpha^2) sum_m Q_mp / L_m   (p >= 1),
+  //   v_0  = beta sum_m Bw_m z_m / L_m,
+  // (1 and 0 when 1/alpha^2 = 0) instead of H0 minus sums that cancel it.
   double H[kDrMaxK][kDrMaxK], v[kDrMaxK], g[kDrMaxK];
   const double* h0 = a.H0 + c * kDrMaxK * kDrMaxK;
 #pragma unroll
@@ -320,9 +328,11 @@ __global__ void __launch_bounds__(128) drift_kernel(const DriftArgs a) {
     g[p] = a.g[c * kDrMaxK + p];
     v[p] = 0.0;
 #pragma unroll
-    for (int q = 0; q <= p; ++q) H[p][q] = h0[p * kDrMaxK + q];
+    for (int q = 0; q <= p; ++q) H[p][q] = q == 0 ? 0.0 : h0[p * kDrMaxK + q];  // column 0: sums of 1/L terms
   }
   const double cal = a.inv_alpha2, beta = a.beta;
+  const bool finite_alpha = cal != 0.0;
+  const double bg0 = K > 0 ? beta * g[0] : 0.0;
   double S = 0.0;
   for (int m = 0; m < M; ++m) {
     double Y, Bw, Q[kDrMaxK];
@@ -340,20 +350,31 @@ __global__ void __launch_bounds__(128) drift_kernel(const DriftArgs a) {
     if (K > 3) Q[3] = bQ3[m * T + tid];
     const double L = Bw + cal;
     if (!(L > 0.0)) continue;  // empty bin with 1/alpha^2 = 0: dropped
-    if (K > 0) Q[0] = beta * Bw;
     const double rL = recip(L);
     double z = Y;
+    if (K > 0) z -= Bw * bg0;
 #pragma unroll
-    for (int p = 0; p < K; ++p) z -= Q[p] * g[p];
+    for (int p = 1; p < K; ++p) z -= Q[p] * g[p];
     const double zl = z * rL;
     S += z * zl;
+    if (K > 0) {
+      v[0] += Bw * zl;
+      if (finite_alpha) H[0][0] += Bw * rL;
+    }
 #pragma unroll
-    for (int p = 0; p < K; ++p) {
+    for (int p = 1; p < K; ++p) {
       v[p] += Q[p] * zl;
       const double qs = Q[p] * rL;
+      if (finite_alpha) H[p][0] += qs;
 #pragma unroll
-      for (int q = 0; q <= p; ++q) H[p][q] -= qs * Q[q];
+      for (int q = 1; q <= p; ++q) H[p][q] -= qs * Q[q];
     }
+  }
+  if (K > 0) {
+    v[0] *= beta;
+    H[0][0] = 1.0 + beta * beta * cal * H[0][0];
+#pragma unroll
+    for (int p = 1; p < K; ++p) H[p][0] *= beta * cal;
   }
   // v^T H^-1 v by Cholesky (H >= I): off-diagonal factors and the forward
   // substitution multiply by the reciprocal square roots of the pivots
