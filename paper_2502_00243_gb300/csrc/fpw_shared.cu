@@ -550,23 +550,38 @@ __global__ void __launch_bounds__(kShThreads, 1) shared_mma_kernel(const SharedA
       const int64_t fbase = f0 + (int64_t)op * fpm;
       const int jmax = (int)((F - fbase) < fpm ? (F - fbase) : fpm);
       const bool cbad = cvalid && a.curve_bad[c];
-      // both lanes of a pair store the even lane's sum to the same address
+      // both lanes of a pair store the pair's sum to the same address
       // (one transaction, no divergent branch before the next shuffle); lanes
       // of padding curves write into a scratch area instead
       float* const s32 = a.S32 ? (cvalid ? a.S32 + c * F + fbase : a.scratch32 + lane * kShMaxFpm) : nullptr;
       double* const s64 = a.S_out ? (cvalid ? a.S_out + c * F + fbase : a.scratch64 + lane * kShMaxFpm) : nullptr;
       const float nan = __int_as_float(0x7fc00000);
-      const int pair_lane = lane & ~1;
+      // this lane's part of the running frequency sum; the two lanes of a
+      // curve's pair add up to the sum
       float acc = 0.f;
       if (!fail) {
-        // lanes 2c and 2c + 1 hold the A and B rows of curve c; the even lane
-        // reduces, the odd lane supplies B by shuffle
+        // lanes 2c and 2c + 1 hold the A and B rows of curve c. For M >= 8 the
+        // pair splits each block of 8 columns: one shuffle per two columns gives
+        // the even lane B of an even column and the odd lane A of an odd one, so
+        // each lane forms the terms A^2 / (B + 1/alpha^2) of its own columns, and
+        // a block holds at most one frequency end. Below 8 bins the even lane
+        // forms every term.
         const float sa = cvalid ? a.inv_scale[2 * c] : 0.f, sw = cvalid ? a.inv_scale[2 * c + 1] : 0.f;
         const int cb = half == 0 ? 0 : split, ce = half == 0 ? split : rows_used;
-        int jl = cb / M, m = cb - jl * M;
+        const int par = lane & 1;
+        int jl = cb / M;
+        int fend = (jl + 1) * M;  // the column where frequency jl ends (warp-uniform)
+        auto emit = [&](float S) {  // frequency jl complete
+          if (half == 1 && straddle && jl == js) {
+            sPart[op * 128 + row] = S;  // the second part of the straddling frequency
+          } else if (jl < jmax) {
+            if (s32) s32[jl] = cbad ? nan : S;
+            if (s64) s64[jl] = cbad ? (double)nan : (double)S;
+          }
+        };
         const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)op * 256u;
-        // 8 columns per step in a compact loop; the next step's TMEM load is
-        // in flight while this step's columns are reduced
+        // 8 columns per step; the next step's TMEM load is in flight while
+        // this step's columns are reduced
         uint32_t nx[8];
         if (nch > 0 && cb < ce) tmem_ld8_issue(tbase + (uint32_t)cb, nx);
         for (int c0 = cb; c0 < ce; c0 += 8) {
@@ -580,38 +595,48 @@ __global__ void __launch_bounds__(kShThreads, 1) shared_mma_kernel(const SharedA
 #pragma unroll
             for (int u = 0; u < 8; ++u) v[u] = 0u;
           }
-          float tv[8];
+          if (M >= 8) {
+            float lo = 0.f, hi = 0.f;  // this lane's terms before / after the frequency end
 #pragma unroll
-          for (int u = 0; u < 8; ++u) {  // independent, branch-free column terms
-            const float val = __uint_as_float(v[u]);
-            const float other = __shfl_xor_sync(0xffffffffu, val, 1);
-            const float A = val * sa;
-            const float den = other * sw + cal;
-            tv[u] = (den >= 1.17549435e-38f && c0 + u < ce) ? (A * A) * rcp_approx(den) : 0.f;
-          }
+            for (int q = 0; q < 4; ++q) {
+              const float ev = __uint_as_float(v[2 * q]), od = __uint_as_float(v[2 * q + 1]);
+              const float recv = __shfl_xor_sync(0xffffffffu, par ? ev : od, 1);
+              const float A = (par ? recv : ev) * sa;
+              const float den = (par ? od : recv) * sw + cal;
+              const int col = c0 + 2 * q + par;
+              const float term = (den >= 1.17549435e-38f && col < ce) ? (A * A) * rcp_approx(den) : 0.f;
+              lo += col < fend ? term : 0.f;
+              hi += col < fend ? 0.f : term;
+            }
+            acc += lo;
+            if (fend <= c0 + 8 && fend <= ce) {
+              emit(acc + __shfl_xor_sync(0xffffffffu, acc, 1));
+              acc = hi;
+              ++jl;
+              fend += M;
+            }
+          } else {
 #pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            acc += tv[u];
-            const bool endf = c0 + u < ce && m + 1 == M;  // warp-uniform
-            if (endf) {
-              const float S = __shfl_sync(0xffffffffu, acc, pair_lane);
-              if (half == 1 && straddle && jl == js) {
-                sPart[op * 128 + row] = S;  // the second part of the straddling frequency
-              } else if (jl < jmax) {
-                if (s32) s32[jl] = cbad ? nan : S;
-                if (s64) s64[jl] = cbad ? (double)nan : (double)S;
+            for (int u = 0; u < 8; ++u) {
+              const float val = __uint_as_float(v[u]);
+              const float other = __shfl_xor_sync(0xffffffffu, val, 1);
+              const float A = val * sa;
+              const float den = other * sw + cal;
+              acc += (par == 0 && den >= 1.17549435e-38f && c0 + u < ce) ? (A * A) * rcp_approx(den) : 0.f;
+              if (c0 + u < ce && c0 + u + 1 == fend) {  // warp-uniform
+                emit(acc + __shfl_xor_sync(0xffffffffu, acc, 1));
+                acc = 0.f;
+                ++jl;
+                fend += M;
               }
             }
-            acc = endf ? 0.f : acc;
-            m = endf ? 0 : m + 1;
-            jl += endf ? 1 : 0;
           }
         }
       }
       fence_before_sync();
       builders_sync(kShBuilders);  // partial sums visible; every TMEM read of this item done
       if (!fail && half == 0 && straddle && js < jmax) {
-        const float S = __shfl_sync(0xffffffffu, acc, pair_lane) + sPart[op * 128 + (row & ~1)];
+        const float S = acc + __shfl_xor_sync(0xffffffffu, acc, 1) + sPart[op * 128 + (row & ~1)];
         if (s32) s32[js] = cbad ? nan : S;
         if (s64) s64[js] = cbad ? (double)nan : (double)S;
       }
@@ -772,16 +797,15 @@ cudaError_t launch_shared(const SharedArgs& a, int nsm, cudaStream_t st) {
   }
   if (a.k > 0 && a.ncurves > 0) {
     DenseTopk32Args t{};
-  t.S32 = a.S32;
-  t.nfreq = a.nfreq;
-  t.k = a.k;
-  t.peak_raw = a.peak_raw;
-  t.curve_bad = a.curve_bad;
-  t.status = a.status;
-  t.topk_idx = a.topk_idx;
-  t.topk_S = a.topk_S;
-  dense_topk32_kernel<<<(unsigned)a.ncurves, kShTopkThreads, 0, st>>>(t);
-    e = cudaGetLastError();
+    t.S32 = a.S32;
+    t.nfreq = a.nfreq;
+    t.k = a.k;
+    t.peak_raw = a.peak_raw;
+    t.curve_bad = a.curve_bad;
+    t.status = a.status;
+    t.topk_idx = a.topk_idx;
+    t.topk_S = a.topk_S;
+    e = launch_dense_topk32(t, a.ncurves, st);
   }
   return e;
 }
