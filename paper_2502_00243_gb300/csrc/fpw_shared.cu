@@ -509,19 +509,38 @@ __global__ void __launch_bounds__(kShThreads, 1) shared_mma_kernel(const SharedA
           const bool obs_ok = ch * kShObs + lane < n;
           const unsigned long long P = sP[ib], D = sD[ib];
           const double tl = sT[ib];
-          for (int e = tid; e < npairs; e += kShBuilders) {
+          // pair e = (frequency e / 32, this lane's observation): clear its
+          // previous one and set its new one; two pairs at a time, both bins
+          // and both previous bins read before any store (the pairs' rows are
+          // disjoint)
+          auto put = [&](int e, unsigned m, unsigned mo) {
             const int j = e >> 5;  // warp-uniform
             const int op = j >= fpm ? 1 : 0;
-            const int jl = j - op * fpm;
-            unsigned m = 0u;
-            if (obs_ok && f0 + j < F)
-              m = bin_of_phase(lin ? P + (unsigned long long)j * D : phase_fixed64(tl, sF[j]), (unsigned)M);
+            const uint32_t r0 = (uint32_t)((j - op * fpm) * M);
             const uint32_t base = lane_off + (uint32_t)op * op_bytes;
-            const uint32_t ro = (uint32_t)(jl * M) + old[e];
-            const uint32_t rn = (uint32_t)(jl * M) + m;
+            const uint32_t ro = r0 + mo, rn = r0 + m;
             *reinterpret_cast<uint32_t*>(hs + base + (ro >> 3) * 256u + (ro & 7u) * 16u) = 0u;
             *reinterpret_cast<uint32_t*>(hs + base + (rn >> 3) * 256u + (rn & 7u) * 16u) = kOneOne;
             old[e] = (uint8_t)m;
+          };
+          if (lin) {
+            for (int e = tid; e < npairs; e += 2 * kShBuilders) {
+              const int e2 = e + kShBuilders;
+              const bool two = e2 < npairs;  // warp-uniform
+              const int ja = e >> 5, jb = e2 >> 5;
+              const unsigned ma = (obs_ok && f0 + ja < F) ? bin_of_phase(P + (unsigned long long)ja * D, (unsigned)M) : 0u;
+              const unsigned mb =
+                  (two && obs_ok && f0 + jb < F) ? bin_of_phase(P + (unsigned long long)jb * D, (unsigned)M) : 0u;
+              const unsigned oa = old[e], ob = two ? old[e2] : 0u;
+              put(e, ma, oa);
+              if (two) put(e2, mb, ob);
+            }
+          } else {
+            for (int e = tid; e < npairs; e += kShBuilders) {
+              const int j = e >> 5;
+              const unsigned m = (obs_ok && f0 + j < F) ? bin_of_phase(phase_fixed64(tl, sF[j]), (unsigned)M) : 0u;
+              put(e, m, old[e]);
+            }
           }
           fence_async_smem();
           __syncwarp();
