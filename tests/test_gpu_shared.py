@@ -160,3 +160,18 @@ def test_shared_irregular_grid(G, ctx):
         assert_S_close(Sd[c], S_or[c], bound, mask=~near, what=f"irregular grid curve {c}")
         o_idx, o_S = oracle.topk(S_or[c], 9)
         check_topk(idx[c], Sk[c], o_idx, o_S, abs_tol=1e-7 * bound, o_dense=S_or[c], what=f"irregular grid curve {c}")
+
+
+@pytest.mark.parametrize("ia2", [1e38, 3e-38])
+def test_shared_extreme_inv_alpha2(G, ctx, ia2):
+    """Bin denominators B_m + 1/alpha^2 near the top of the float32 range (the
+    reciprocal's result subnormal) and 1/alpha^2 at the bottom: S against the
+    oracle, finite everywhere."""
+    t, x, sigma, freqs = field(6, 20, 300, 700)
+    p = G.fpw_params_default(inv_alpha2=ia2)
+    _, _, Sd, st = run_shared(G, ctx, t, x, sigma, freqs, 12, 0, params=p)
+    assert st == 0 and np.isfinite(Sd).all()
+    S_or = oracle.fpw_shared(t, x, sigma, freqs, 12, ia2)
+    near = oracle.min_edge(t, freqs, 12) <= 1e-9
+    for c in range(20):
+        assert_S_close(Sd[c], S_or[c], s_bound(x[c], sigma[c]), mask=~near, what=f"ia2={ia2:g} curve {c}")
