@@ -187,9 +187,12 @@ int choose_shape(fpw_ctx* ctx, const fpw_params& p, int M, int k, int64_t max_n,
     R = 8;
   else if (M <= 24)
     R = n_typ < 300 ? 2 : 4;
-  else if (M <= 50)
+  else if (M <= 32 || (M <= 50 && ngroups == 0))
     R = 2;
-  else if (M <= 64) {  // two blocks of 6 warps per SM (T = 128, R = 2 leaves one block of 4)
+  else if (M <= 50) {  // several M: the per-frequency combination favours more warps
+    T = 256;
+    R = 1;
+  } else if (M <= 64) {  // two blocks of 6 warps per SM (T = 128, R = 2 leaves one block of 4)
     T = 192;
     R = 1;
   } else

@@ -41,6 +41,7 @@ def run_multi(G, ctx, w, M_max, groups, k, params=None):
     (20, [1, 2, 4, 5, 10], [0, 50, 700, 1500, 3100], 3000),
     (60, [3, 6, 15], [400, 1200], 2048),
     (12, [12, 1, 3], [90, 333], 1021),
+    (40, [2, 4, 10], [700, 64, 1500], 1500),
 ])
 def test_multi_m_dense_topk_and_offsets(G, M_max, groups, ns, F):
     w = L.ragged(60 + M_max, ns, F, M=M_max, k=5)
