@@ -17,9 +17,12 @@
 //   H = H0 - sum_m Q_m Q_m^T / L_m   (symmetric positive definite, >= I).
 //
 // Bins with no observation and 1/alpha^2 = 0 are dropped (their rows vanish).
-// B_0 = beta T_0 = beta is constant, so Q_m0 = beta Bw_m needs no sum of its
-// own: a bin holds Y, Bw and Q_m1..Q_m(K-1), 1 + max(K, 1) floats; the row of
-// H and the entry of v that belong to B_0 take closed forms in the bin sums.
+// Since z_m = sum over bin m of w (x - B g), the bins accumulate the residuals
+// of the baseline fit (formed per observation in binary64) and hold z_m
+// itself: a drift far above the noise never enters an FP32 sum. B_0 = beta T_0
+// = beta is constant, so Q_m0 = beta Bw_m needs no sum of its own: a bin holds
+// z, Bw and Q_m1..Q_m(K-1), 1 + max(K, 1) floats; the row of H and the entry of
+// v that belong to B_0 take closed forms in the bin sums.
 // The sums accumulate in FP32 in thread-private shared-memory bins (one thread
 // per frequency, packed as float2 / float4 / float4 + float), phases are the
 // exact 64-bit anchors of the tile kernels stepped across a tile of
@@ -37,7 +40,7 @@ constexpr int kDrChunk = 128;  // observations staged at a time
 
 // Per observation, written once by the prep kernel.
 struct DriftObs {
-  float4 q;                // w x, w, w B_1, w B_2
+  float4 q;                // w (x - B g) (w x for K = 0), w, w B_1, w B_2
   unsigned long long D;    // frac(t df) as 64-bit fixed point (linear grids)
   float q3;                // w B_3
   float pad;
@@ -59,6 +62,26 @@ __device__ __forceinline__ double recip(double L) {
   return fma(r0, fma(-L, r0, 1.0), r0);
 }
 
+// B[k] = beta T_k(tau), k < kDrMaxK (Chebyshev polynomials of the first kind).
+__device__ __forceinline__ void chebyshev(double tau, double beta, double (&Bk)[kDrMaxK]) {
+  double tkm1 = 1.0, tk = tau;
+#pragma unroll
+  for (int k = 0; k < kDrMaxK; ++k) {
+    double T;
+    if (k == 0) {
+      T = 1.0;
+    } else if (k == 1) {
+      T = tau;
+    } else {
+      const double tn = 2.0 * tau * tk - tkm1;
+      tkm1 = tk;
+      tk = tn;
+      T = tn;
+    }
+    Bk[k] = beta * T;
+  }
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -70,6 +93,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 __global__ void __launch_bounds__(256) drift_prep_kernel(const DriftArgs a) {
   __shared__ double red[8][kDrMaxK * kDrMaxK + kDrMaxK + 3];
   __shared__ double tl[2];
+  __shared__ double sg[kDrMaxK];
   const int64_t c = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int K = a.K;
@@ -128,22 +152,7 @@ __global__ void __launch_bounds__(256) drift_prep_kernel(const DriftArgs a) {
     }
     const double tau = (span > 0.0) ? 2.0 * (a.t[o0 + i] - lo) / span - 1.0 : 0.0;
     double Bk[kDrMaxK];
-    double tkm1 = 1.0, tk = tau;
-#pragma unroll
-    for (int k = 0; k < kDrMaxK; ++k) {
-      double T;
-      if (k == 0) {
-        T = 1.0;
-      } else if (k == 1) {
-        T = tau;
-      } else {
-        const double tn = 2.0 * tau * tk - tkm1;
-        tkm1 = tk;
-        tk = tn;
-        T = tn;
-      }
-      Bk[k] = a.beta * T;
-    }
+    chebyshev(tau, a.beta, Bk);
     float wb[kDrMaxK];
 #pragma unroll
     for (int k = 0; k < kDrMaxK; ++k) {
@@ -203,7 +212,24 @@ __global__ void __launch_bounds__(256) drift_prep_kernel(const DriftArgs a) {
       g[k] = s / Lc[k][k];
     }
     for (int k = K; k < kDrMaxK; ++k) g[k] = 0.0;
+    for (int k = 0; k < kDrMaxK; ++k) sg[k] = g[k];
   }
+  __syncthreads();
+  // The bins sum w (x - B g), the residuals of the curve's baseline fit: their
+  // bin sums are z_m = Y_m - Q_m . g itself, so a drift far above the noise
+  // does not cancel inside FP32 sums of w x.
+  if (K > 0 && !cbad)
+    for (int64_t i = tid; i < n; i += blockDim.x) {
+      const double s = a.sigma[o0 + i];
+      const double tau = (span > 0.0) ? 2.0 * (a.t[o0 + i] - lo) / span - 1.0 : 0.0;
+      double Bk[kDrMaxK];
+      chebyshev(tau, a.beta, Bk);
+      double r = a.x[o0 + i];
+#pragma unroll
+      for (int k = 0; k < kDrMaxK; ++k)
+        if (k < K) r -= Bk[k] * sg[k];
+      reinterpret_cast<DriftObs*>(a.payload)[o0 + i].q.x = (float)(r / (s * s));
+    }
   if (blockIdx.x == 0)
     for (int64_t q = tid; q < a.nfreq; q += blockDim.x)
       if (!isfinite(a.freqs[q])) atomicOr(a.status, kStatusGrid);
@@ -321,18 +347,16 @@ __global__ void __launch_bounds__(128) drift_kernel(const DriftArgs a) {
   //   H_p0 = beta (1/alpha^2) sum_m Q_mp / L_m   (p >= 1),
   //   v_0  = beta sum_m Bw_m z_m / L_m,
   // (1 and 0 when 1/alpha^2 = 0) instead of H0 minus sums that cancel it.
-  double H[kDrMaxK][kDrMaxK], v[kDrMaxK], g[kDrMaxK];
+  double H[kDrMaxK][kDrMaxK], v[kDrMaxK];
   const double* h0 = a.H0 + c * kDrMaxK * kDrMaxK;
 #pragma unroll
   for (int p = 0; p < K; ++p) {
-    g[p] = a.g[c * kDrMaxK + p];
     v[p] = 0.0;
 #pragma unroll
     for (int q = 0; q <= p; ++q) H[p][q] = q == 0 ? 0.0 : h0[p * kDrMaxK + q];  // column 0: sums of 1/L terms
   }
   const double cal = a.inv_alpha2, beta = a.beta;
   const bool finite_alpha = cal != 0.0;
-  const double bg0 = K > 0 ? beta * g[0] : 0.0;
   double S = 0.0;
   for (int m = 0; m < M; ++m) {
     double Y, Bw, Q[kDrMaxK];
@@ -351,10 +375,7 @@ __global__ void __launch_bounds__(128) drift_kernel(const DriftArgs a) {
     const double L = Bw + cal;
     if (!(L > 0.0)) continue;  // empty bin with 1/alpha^2 = 0: dropped
     const double rL = recip(L);
-    double z = Y;
-    if (K > 0) z -= Bw * bg0;
-#pragma unroll
-    for (int p = 1; p < K; ++p) z -= Q[p] * g[p];
+    const double z = Y;  // the bin's sum of w (x - B g)
     const double zl = z * rL;
     S += z * zl;
     if (K > 0) {

@@ -169,3 +169,39 @@ def test_drift_irregular_grid(G, ctx):
         assert_S_close(Sd[c], S_or, bound, mask=~near, what=f"irregular grid curve {c}")
         o_idx, o_S = oracle.topk(S_or, 8)
         check_topk(idx[c], Sk[c], o_idx, o_S, abs_tol=1e-7 * bound, o_dense=S_or, what=f"irregular grid curve {c}")
+
+
+def drifting(seed, ns, F, K):
+    """Ragged curves with a polynomial baseline of ~100 noise sigmas added
+    (degree K - 1 in the curve's scaled time, random coefficients)."""
+    w = L.ragged(seed, ns, F, M=16, k=3)
+    rng = np.random.default_rng([17, seed])
+    x = w.x.copy()
+    for c in range(w.ncurves):
+        a, b = w.offsets[c], w.offsets[c + 1]
+        t, s = w.t[a:b], w.sigma[a:b]
+        tau = 2.0 * (t - t.min()) / np.ptp(t) - 1.0
+        coef = rng.uniform(-1.0, 1.0, 3) * 100.0 * np.median(s)
+        x[a:b] += coef[0] * tau + coef[1] * (2 * tau ** 2 - 1) + (coef[2] * (4 * tau ** 3 - 3 * tau) if K >= 4 else 0.0)
+    w.x = x
+    return w
+
+
+@pytest.mark.parametrize("K,beta", [(2, 1.0), (3, 1.0), (4, 0.5)])
+def test_drift_strong_baseline(G, ctx, K, beta):
+    """A baseline ~100 noise sigmas tall, where marginalising it matters most.
+    The bins sum the residuals of the curve's baseline fit, so the FP32 sums
+    never carry the drift itself; the absolute floor is 1e-9 sum w x^2 (about
+    1e-5 of the noise chi^2 here), far below what FP32 sums of w x would
+    reach."""
+    w = drifting(400 + K, [700, 1200, 90], 600, K)
+    idx, Sk, Sd, st = run_drift(G, ctx, w, 16, K, beta, 3)
+    assert st == 0
+    for c in range(w.ncurves):
+        t, x, s = w.curve(c)
+        S_or = oracle.fpw_drift(t, x, s, w.freqs, 16, K, beta)
+        bound = s_bound(x, s)
+        near = oracle.min_edge(t, w.freqs, 16) <= 1e-9
+        assert_S_close(Sd[c], S_or, bound, absf=1e-9, mask=~near, what=f"K={K} drifting curve {c}")
+        o_idx, o_S = oracle.topk(S_or, 7)
+        check_topk(idx[c], Sk[c], o_idx, o_S, abs_tol=1e-9 * bound, o_dense=S_or, what=f"K={K} drifting curve {c}")
