@@ -82,6 +82,20 @@ __device__ __forceinline__ void chebyshev(double tau, double beta, double (&Bk)[
   }
 }
 
+// float -> double from the IEEE 754 layouts with integer operations (exact for
+// normal numbers and zero; subnormal, infinite and NaN inputs take the
+// hardware conversion).
+__device__ __forceinline__ double widen(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xFFu;
+  if (e == 0u || e == 0xFFu) {
+    if ((u & 0x7FFFFFFFu) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
+    return (double)f;
+  }
+  const unsigned hi = ((u & 0x80000000u) | ((u & 0x7FFFFFFFu) >> 3)) + (896u << 20);
+  return __hiloint2double((int)hi, (int)(u << 29));
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -362,16 +376,16 @@ __global__ void __launch_bounds__(128) drift_kernel(const DriftArgs a) {
     double Y, Bw, Q[kDrMaxK];
     if (kWide) {
       const float4 b = reinterpret_cast<const float4*>(bins)[m * T + tid];
-      Y = b.x;
-      Bw = b.y;
-      Q[1] = b.z;
-      if (K > 2) Q[2] = b.w;
+      Y = widen(b.x);
+      Bw = widen(b.y);
+      Q[1] = widen(b.z);
+      if (K > 2) Q[2] = widen(b.w);
     } else {
       const float2 b = reinterpret_cast<const float2*>(bins)[m * T + tid];
-      Y = b.x;
-      Bw = b.y;
+      Y = widen(b.x);
+      Bw = widen(b.y);
     }
-    if (K > 3) Q[3] = bQ3[m * T + tid];
+    if (K > 3) Q[3] = widen(bQ3[m * T + tid]);
     const double L = Bw + cal;
     if (!(L > 0.0)) continue;  // empty bin with 1/alpha^2 = 0: dropped
     const double rL = recip(L);
