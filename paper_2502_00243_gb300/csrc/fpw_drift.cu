@@ -53,12 +53,27 @@ __host__ __device__ constexpr int drift_stage_bytes(int K) { return 16 + 16 + (K
 // float4 for K = 2, 3, and Q_3 in a float of its own for K = 4.
 __host__ __device__ constexpr int drift_bin_bytes(int K) { return K <= 1 ? 8 : (K <= 3 ? 16 : 20); }
 
-// 1/L in binary64 from the FP32 reciprocal and one Newton-Raphson step
-// (r <- r + r (1 - L r)), which squares the FP32 estimate's relative error to
-// ~2^-46; an exact division where L lies outside [2^-100, 2^100].
-__device__ __forceinline__ double recip(double L) {
-  if (!(L > 0x1p-100 && L < 0x1p100)) return 1.0 / L;
-  const double r0 = (double)__frcp_rn((float)L);
+// float -> double from the IEEE 754 layouts with integer operations (exact for
+// normal numbers and zero; subnormal, infinite and NaN inputs take the
+// hardware conversion).
+__device__ __forceinline__ double widen(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xFFu;
+  if (e == 0u || e == 0xFFu) {
+    if ((u & 0x7FFFFFFFu) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
+    return (double)f;
+  }
+  const unsigned hi = ((u & 0x80000000u) | ((u & 0x7FFFFFFFu) >> 3)) + (896u << 20);
+  return __hiloint2double((int)hi, (int)(u << 29));
+}
+
+// 1/L in binary64 from the FP32 reciprocal of Lf (L formed in FP32) and one
+// Newton-Raphson step (r <- r + r (1 - L r)), which squares the FP32
+// estimate's relative error to ~2^-45; an exact division where Lf lies
+// outside [2^-100, 2^100].
+__device__ __forceinline__ double recip(double L, float Lf) {
+  if (!(Lf > 0x1p-100f && Lf < 0x1p100f)) return 1.0 / L;
+  const double r0 = widen(__frcp_rn(Lf));
   return fma(r0, fma(-L, r0, 1.0), r0);
 }
 
@@ -80,20 +95,6 @@ __device__ __forceinline__ void chebyshev(double tau, double beta, double (&Bk)[
     }
     Bk[k] = beta * T;
   }
-}
-
-// float -> double from the IEEE 754 layouts with integer operations (exact for
-// normal numbers and zero; subnormal, infinite and NaN inputs take the
-// hardware conversion).
-__device__ __forceinline__ double widen(float f) {
-  const unsigned u = __float_as_uint(f);
-  const unsigned e = (u >> 23) & 0xFFu;
-  if (e == 0u || e == 0xFFu) {
-    if ((u & 0x7FFFFFFFu) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
-    return (double)f;
-  }
-  const unsigned hi = ((u & 0x80000000u) | ((u & 0x7FFFFFFFu) >> 3)) + (896u << 20);
-  return __hiloint2double((int)hi, (int)(u << 29));
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -370,25 +371,28 @@ __global__ void __launch_bounds__(128) drift_kernel(const DriftArgs a) {
     for (int q = 0; q <= p; ++q) H[p][q] = q == 0 ? 0.0 : h0[p * kDrMaxK + q];  // column 0: sums of 1/L terms
   }
   const double cal = a.inv_alpha2, beta = a.beta;
+  const float calf = (float)cal;
   const bool finite_alpha = cal != 0.0;
   double S = 0.0;
   for (int m = 0; m < M; ++m) {
     double Y, Bw, Q[kDrMaxK];
+    float bwf;
     if (kWide) {
       const float4 b = reinterpret_cast<const float4*>(bins)[m * T + tid];
       Y = widen(b.x);
-      Bw = widen(b.y);
+      bwf = b.y;
       Q[1] = widen(b.z);
       if (K > 2) Q[2] = widen(b.w);
     } else {
       const float2 b = reinterpret_cast<const float2*>(bins)[m * T + tid];
       Y = widen(b.x);
-      Bw = widen(b.y);
+      bwf = b.y;
     }
+    Bw = widen(bwf);
     if (K > 3) Q[3] = widen(bQ3[m * T + tid]);
     const double L = Bw + cal;
     if (!(L > 0.0)) continue;  // empty bin with 1/alpha^2 = 0: dropped
-    const double rL = recip(L);
+    const double rL = recip(L, bwf + calf);
     const double z = Y;  // the bin's sum of w (x - B g)
     const double zl = z * rL;
     S += z * zl;
