@@ -204,7 +204,11 @@ FPW_API int fpw_periodogram_shared(fpw_ctx* ctx, void* stream, const fpw_params*
  *       memory per block, b = 8 (K <= 1), 16 (K = 2, 3) or 20 (K = 4) bytes
  *       per bin (FPW_ENOTSUP beyond)
  * params: FPW_PHASE_FIXED64 and FPW_ACCUM_FP32 only; inv_alpha2 and
- * peak_mode apply. Scratch held by the context: 32 bytes per observation,
+ * peak_mode apply; threads (32..128) and freqs_per_thread (1 or 2) set the
+ * block shape (0 = 128 threads, fewer where M needs it, and two frequencies
+ * per thread for K <= 1 where they fit); a shape whose bins do not fit (R
+ * times the bound on M above) or any other value gives FPW_ENOTSUP.
+ * Scratch held by the context: 32 bytes per observation,
  * 168 bytes per curve and,
  * when k > 0, a dense FP32 periodogram of 4 ncurves nfreq bytes. Reads
  * offsets[ncurves] back to the host (synchronizes `stream` once).

@@ -250,6 +250,100 @@ __global__ void __launch_bounds__(256) drift_prep_kernel(const DriftArgs a) {
       if (!isfinite(a.freqs[q])) atomicOr(a.status, kStatusGrid);
 }
 
+// The binary64 reduction of one frequency from its bins (slots slot0 + m T):
+// S = sum z^2 / L + v^T H^-1 v, H kept as its lower triangle. The constant
+// basis function B_0 = beta has Q_m0 = beta Bw_m, and sum_i w_i B_ip =
+// sum_m Q_mp, so its row of H and its entry of v take closed forms in the bin
+// sums,
+//   H_00 = 1 + beta^2 (1/alpha^2) sum_m Bw_m / L_m,
+//   H_p0 = beta (1/alpha^2) sum_m Q_mp / L_m   (p >= 1),
+//   v_0  = beta sum_m Bw_m z_m / L_m,
+// (1 and 0 when 1/alpha^2 = 0) instead of H0 minus sums that cancel it.
+template <int K>
+__device__ __forceinline__ double drift_reduce(const DriftArgs& a, const unsigned char* bins, const float* bQ3,
+                                               int slot0, int T, int64_t c) {
+  constexpr bool kWide = K >= 2;
+  const int M = a.M;
+  double H[kDrMaxK][kDrMaxK], v[kDrMaxK];
+  const double* h0 = a.H0 + c * kDrMaxK * kDrMaxK;
+#pragma unroll
+  for (int p = 0; p < K; ++p) {
+    v[p] = 0.0;
+#pragma unroll
+    for (int q = 0; q <= p; ++q) H[p][q] = q == 0 ? 0.0 : h0[p * kDrMaxK + q];  // column 0: sums of 1/L terms
+  }
+  const double cal = a.inv_alpha2, beta = a.beta;
+  const float calf = (float)cal;
+  const bool finite_alpha = cal != 0.0;
+  double S = 0.0;
+  for (int m = 0; m < M; ++m) {
+    const int sl = slot0 + m * T;
+    double Y, Bw, Q[kDrMaxK];
+    float bwf;
+    if (kWide) {
+      const float4 b = reinterpret_cast<const float4*>(bins)[sl];
+      Y = widen(b.x);
+      bwf = b.y;
+      Q[1] = widen(b.z);
+      if (K > 2) Q[2] = widen(b.w);
+    } else {
+      const float2 b = reinterpret_cast<const float2*>(bins)[sl];
+      Y = widen(b.x);
+      bwf = b.y;
+    }
+    Bw = widen(bwf);
+    if (K > 3) Q[3] = widen(bQ3[sl]);
+    const double L = Bw + cal;
+    if (!(L > 0.0)) continue;  // empty bin with 1/alpha^2 = 0: dropped
+    const double rL = recip(L, bwf + calf);
+    const double z = Y;  // the bin's sum of w (x - B g)
+    const double zl = z * rL;
+    S += z * zl;
+    if (K > 0) {
+      v[0] += Bw * zl;
+      if (finite_alpha) H[0][0] += Bw * rL;
+    }
+#pragma unroll
+    for (int p = 1; p < K; ++p) {
+      v[p] += Q[p] * zl;
+      const double qs = Q[p] * rL;
+      if (finite_alpha) H[p][0] += qs;
+#pragma unroll
+      for (int q = 1; q <= p; ++q) H[p][q] -= qs * Q[q];
+    }
+  }
+  if (K > 0) {
+    v[0] *= beta;
+    H[0][0] = 1.0 + beta * beta * cal * H[0][0];
+#pragma unroll
+    for (int p = 1; p < K; ++p) H[p][0] *= beta * cal;
+  }
+  // v^T H^-1 v by Cholesky (H >= I): off-diagonal factors and the forward
+  // substitution multiply by the reciprocal square roots of the pivots
+  double Lc[kDrMaxK][kDrMaxK], di[kDrMaxK], y[kDrMaxK];
+#pragma unroll
+  for (int p = 0; p < K; ++p)
+#pragma unroll
+    for (int q = 0; q <= p; ++q) {
+      double s = H[p][q];
+#pragma unroll
+      for (int r = 0; r < q; ++r) s -= Lc[p][r] * Lc[q][r];
+      if (p == q)
+        di[p] = s > 0.0 ? rsqrt(s) : 0.0;
+      else
+        Lc[p][q] = s * di[q];
+    }
+#pragma unroll
+  for (int p = 0; p < K; ++p) {
+    double s = v[p];
+#pragma unroll
+    for (int r = 0; r < p; ++r) s -= Lc[p][r] * y[r];
+    y[p] = s * di[p];
+    S += y[p] * y[p];
+  }
+  return S;
+}
+
 // One block per (tile of T frequencies, curve); thread = frequency. Bins
 // thread-private (bank = lane), [M][T] slots of drift_bin_bytes(K): one packed
 // read-modify-write per evaluation for K <= 3 (two for K = 4), two
@@ -354,96 +448,181 @@ __global__ void __launch_bounds__(128) drift_kernel(const DriftArgs a) {
     }
   }
   if (k >= F) return;
-  // binary64 reduction: S = sum z^2 / L + v^T H^-1 v, H kept as its lower
-  // triangle. The constant basis function B_0 = beta has Q_m0 = beta Bw_m, and
-  // sum_i w_i B_ip = sum_m Q_mp, so its row of H and its entry of v take
-  // closed forms in the bin sums,
-  //   H_00 = 1 + beta^2 (1/alpha^2) sum_m Bw_m / L_m,
-  //   H_p0 = beta (1/alpha^2) sum_m Q_mp / L_m   (p >= 1),
-  //   v_0  = beta sum_m Bw_m z_m / L_m,
-  // (1 and 0 when 1/alpha^2 = 0) instead of H0 minus sums that cancel it.
-  double H[kDrMaxK][kDrMaxK], v[kDrMaxK];
-  const double* h0 = a.H0 + c * kDrMaxK * kDrMaxK;
-#pragma unroll
-  for (int p = 0; p < K; ++p) {
-    v[p] = 0.0;
-#pragma unroll
-    for (int q = 0; q <= p; ++q) H[p][q] = q == 0 ? 0.0 : h0[p * kDrMaxK + q];  // column 0: sums of 1/L terms
-  }
-  const double cal = a.inv_alpha2, beta = a.beta;
-  const float calf = (float)cal;
-  const bool finite_alpha = cal != 0.0;
-  double S = 0.0;
-  for (int m = 0; m < M; ++m) {
-    double Y, Bw, Q[kDrMaxK];
-    float bwf;
-    if (kWide) {
-      const float4 b = reinterpret_cast<const float4*>(bins)[m * T + tid];
-      Y = widen(b.x);
-      bwf = b.y;
-      Q[1] = widen(b.z);
-      if (K > 2) Q[2] = widen(b.w);
-    } else {
-      const float2 b = reinterpret_cast<const float2*>(bins)[m * T + tid];
-      Y = widen(b.x);
-      bwf = b.y;
-    }
-    Bw = widen(bwf);
-    if (K > 3) Q[3] = widen(bQ3[m * T + tid]);
-    const double L = Bw + cal;
-    if (!(L > 0.0)) continue;  // empty bin with 1/alpha^2 = 0: dropped
-    const double rL = recip(L, bwf + calf);
-    const double z = Y;  // the bin's sum of w (x - B g)
-    const double zl = z * rL;
-    S += z * zl;
-    if (K > 0) {
-      v[0] += Bw * zl;
-      if (finite_alpha) H[0][0] += Bw * rL;
-    }
-#pragma unroll
-    for (int p = 1; p < K; ++p) {
-      v[p] += Q[p] * zl;
-      const double qs = Q[p] * rL;
-      if (finite_alpha) H[p][0] += qs;
-#pragma unroll
-      for (int q = 1; q <= p; ++q) H[p][q] -= qs * Q[q];
-    }
-  }
-  if (K > 0) {
-    v[0] *= beta;
-    H[0][0] = 1.0 + beta * beta * cal * H[0][0];
-#pragma unroll
-    for (int p = 1; p < K; ++p) H[p][0] *= beta * cal;
-  }
-  // v^T H^-1 v by Cholesky (H >= I): off-diagonal factors and the forward
-  // substitution multiply by the reciprocal square roots of the pivots
-  double Lc[kDrMaxK][kDrMaxK], di[kDrMaxK], y[kDrMaxK];
-#pragma unroll
-  for (int p = 0; p < K; ++p)
-#pragma unroll
-    for (int q = 0; q <= p; ++q) {
-      double s = H[p][q];
-#pragma unroll
-      for (int r = 0; r < q; ++r) s -= Lc[p][r] * Lc[q][r];
-      if (p == q)
-        di[p] = s > 0.0 ? rsqrt(s) : 0.0;
-      else
-        Lc[p][q] = s * di[q];
-    }
-#pragma unroll
-  for (int p = 0; p < K; ++p) {
-    double s = v[p];
-#pragma unroll
-    for (int r = 0; r < p; ++r) s -= Lc[p][r] * y[r];
-    y[p] = s * di[p];
-    S += y[p] * y[p];
-  }
+  const double S = drift_reduce<K>(a, bins, bQ3, tid, T, c);
   const float Sf = cbad ? __int_as_float(0x7fc00000) : (float)S;
   if (a.S32) a.S32[c * F + k] = Sf;
   if (a.S_out) a.S_out[c * F + k] = cbad ? (double)Sf : S;
 }
 
-const void* drift_fn(int K) {
+// As drift_kernel, with R consecutive frequencies per thread: tiles of T R
+// frequencies, [r][M][T] bin slots, each staged observation serving the
+// thread's R frequencies (half the broadcast per evaluation for R = 2, twice
+// the bins per thread). A separate kernel: the one-frequency loop above runs
+// faster in its own form.
+template <int K, int R>
+__global__ void __launch_bounds__(128) drift_kernel_rf(const DriftArgs a) {
+  constexpr bool kWide = K >= 2;  // (Y, Bw, Q_1, Q_2) as float4, else (Y, Bw) as float2
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int T = blockDim.x, tid = threadIdx.x;
+  const int M = a.M, MT = M * T;
+  const int64_t c = blockIdx.y, F = a.nfreq;
+  const int64_t f0 = (int64_t)blockIdx.x * (T * R);
+  const int j0 = tid * R;  // the thread's first frequency within the tile
+  unsigned char* const bins = smem;                                                         // [R][M][T] main slots
+  float* const bQ3 = reinterpret_cast<float*>(bins + (size_t)R * MT * (kWide ? 16 : 8));    // [R][M][T] (K = 4)
+  ulonglong2* const sPD = reinterpret_cast<ulonglong2*>(smem + (size_t)R * MT * drift_bin_bytes(K));  // [chunk]
+  float4* const sQ = reinterpret_cast<float4*>(sPD + kDrChunk);                             // [chunk]
+  float* const sQ3 = reinterpret_cast<float*>(sQ + kDrChunk);                               // [chunk] (K = 4)
+  const bool grid_bad = (*(volatile unsigned*)a.status & kStatusGrid) != 0u;
+  if (grid_bad) return;
+  const bool cbad = a.curve_bad[c] != 0;
+  const int64_t o0 = a.offsets[c], n = a.offsets[c + 1] - o0;
+  const double df = (F > 1) ? (a.freqs[F - 1] - a.freqs[0]) / (double)(F - 1) : 0.0;
+  const double fa = a.freqs[f0];
+  // linear grid over this tile (the tile kernels' bound on the phase error)?
+  const double tm = a.tabs[c];
+  double fk[R];
+  bool nonlin = false;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int64_t k = f0 + j0 + r;
+    fk[r] = k < F ? a.freqs[k] : fa;
+    if (k < F && fabs(fk[r] - fma((double)(j0 + r), df, fa)) * tm > kGridTolCycles) nonlin = true;
+  }
+  const bool lin = !__syncthreads_or(nonlin);
+  for (int q = 0; q < R * M; ++q) {
+    if (kWide)
+      reinterpret_cast<float4*>(bins)[q * T + tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+    else
+      reinterpret_cast<float2*>(bins)[q * T + tid] = make_float2(0.f, 0.f);
+    if (K > 3) bQ3[q * T + tid] = 0.f;
+  }
+  const DriftObs* const obs = reinterpret_cast<const DriftObs*>(a.payload) + o0;
+  for (int64_t oc = 0; oc < n; oc += kDrChunk) {
+    const int cnt = (int)((n - oc) < kDrChunk ? (n - oc) : kDrChunk);
+    __syncthreads();
+    for (int i = tid; i < cnt; i += T) {
+      const double ti = a.t[o0 + oc + i];
+      const DriftObs ob = obs[oc + i];
+      sPD[i] = lin ? make_ulonglong2(phase_fixed64(ti, fa), ob.D)
+                   : make_ulonglong2((unsigned long long)__double_as_longlong(ti), 0ull);
+      sQ[i] = ob.q;
+      if (K > 3) sQ3[i] = ob.q3;
+    }
+    __syncthreads();
+    if (!cbad) {
+      // the observation's slot for each of the thread's R frequencies
+      auto slots = [&](const ulonglong2 pd, int (&sl)[R]) {
+        if (lin) {
+          unsigned long long phi = pd.x + (unsigned long long)j0 * pd.y;
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            sl[r] = r * MT + (int)bin_of_phase(phi, (unsigned)M) * T + tid;
+            phi += pd.y;
+          }
+        } else {
+          const double ti = __longlong_as_double((long long)pd.x);
+#pragma unroll
+          for (int r = 0; r < R; ++r) sl[r] = r * MT + (int)bin_of_phase(phase_fixed64(ti, fk[r]), (unsigned)M) * T + tid;
+        }
+      };
+      // two observations per iteration: all read-modify-write chains are in
+      // flight at once; where both observations fall in one bin the second
+      // update starts from the first one's sum (same additions in the same order)
+      int i = 0;
+      for (; i + 1 < cnt; i += 2) {
+        int sa[R], sb[R];
+        slots(sPD[i], sa);
+        slots(sPD[i + 1], sb);
+        const float4 pa = sQ[i], pb = sQ[i + 1];
+        if (kWide) {
+          float4* const b4 = reinterpret_cast<float4*>(bins);
+          float4 va[R], vb[R];
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            va[r] = b4[sa[r]];
+            vb[r] = b4[sb[r]];
+          }
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            const float4 ua = make_float4(va[r].x + pa.x, va[r].y + pa.y, va[r].z + pa.z, va[r].w + pa.w);
+            const float4 wb = sa[r] == sb[r] ? ua : vb[r];
+            b4[sa[r]] = ua;
+            b4[sb[r]] = make_float4(wb.x + pb.x, wb.y + pb.y, wb.z + pb.z, wb.w + pb.w);
+          }
+        } else {
+          float2* const b2 = reinterpret_cast<float2*>(bins);
+          float2 va[R], vb[R];
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            va[r] = b2[sa[r]];
+            vb[r] = b2[sb[r]];
+          }
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            const float2 ua = make_float2(va[r].x + pa.x, va[r].y + pa.y);
+            const float2 wb = sa[r] == sb[r] ? ua : vb[r];
+            b2[sa[r]] = ua;
+            b2[sb[r]] = make_float2(wb.x + pb.x, wb.y + pb.y);
+          }
+        }
+        if (K > 3) {
+          const float ra = sQ3[i], rb = sQ3[i + 1];
+          float qa[R], qb[R];
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            qa[r] = bQ3[sa[r]];
+            qb[r] = bQ3[sb[r]];
+          }
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            const float ua = qa[r] + ra;
+            bQ3[sa[r]] = ua;
+            bQ3[sb[r]] = (sa[r] == sb[r] ? ua : qb[r]) + rb;
+          }
+        }
+      }
+      if (i < cnt) {
+        int sa[R];
+        slots(sPD[i], sa);
+        const float4 pa = sQ[i];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          if (kWide) {
+            float4* const b4 = reinterpret_cast<float4*>(bins);
+            const float4 va = b4[sa[r]];
+            b4[sa[r]] = make_float4(va.x + pa.x, va.y + pa.y, va.z + pa.z, va.w + pa.w);
+          } else {
+            float2* const b2 = reinterpret_cast<float2*>(bins);
+            const float2 va = b2[sa[r]];
+            b2[sa[r]] = make_float2(va.x + pa.x, va.y + pa.y);
+          }
+          if (K > 3) bQ3[sa[r]] += sQ3[i];
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int64_t k = f0 + j0 + r;
+    if (k >= F) break;
+    const double S = drift_reduce<K>(a, bins, bQ3, r * MT + tid, T, c);
+    const float Sf = cbad ? __int_as_float(0x7fc00000) : (float)S;
+    if (a.S32) a.S32[c * F + k] = Sf;
+    if (a.S_out) a.S_out[c * F + k] = cbad ? (double)Sf : S;
+  }
+}
+
+const void* drift_fn(int K, int R) {
+  if (R == 2) {
+    switch (K) {
+      case 0: return reinterpret_cast<const void*>(&drift_kernel_rf<0, 2>);
+      case 1: return reinterpret_cast<const void*>(&drift_kernel_rf<1, 2>);
+      case 2: return reinterpret_cast<const void*>(&drift_kernel_rf<2, 2>);
+      case 3: return reinterpret_cast<const void*>(&drift_kernel_rf<3, 2>);
+      default: return reinterpret_cast<const void*>(&drift_kernel_rf<4, 2>);
+    }
+  }
   switch (K) {
     case 0: return reinterpret_cast<const void*>(&drift_kernel<0>);
     case 1: return reinterpret_cast<const void*>(&drift_kernel<1>);
@@ -459,19 +638,23 @@ const void* drift_fn(int K) {
 // static shared memory.
 static size_t drift_dynamic_limit(int smem_optin) {
   cudaFuncAttributes fa{};
-  if (cudaFuncGetAttributes(&fa, drift_fn(4)) != cudaSuccess) return 0;
+  if (cudaFuncGetAttributes(&fa, drift_fn(4, 2)) != cudaSuccess) return 0;
   return smem_optin > (int)fa.sharedSizeBytes ? (size_t)(smem_optin - (int)fa.sharedSizeBytes) : 0;
 }
 
 int drift_threads(int M, int K, int smem_optin) {
   const size_t lim = drift_dynamic_limit(smem_optin);
   for (int T = 128; T >= 32; T >>= 1)
-    if (drift_smem_bytes(M, K, T) <= lim) return T;
+    if (drift_smem_bytes(M, K, T, 1) <= lim) return T;
   return 0;
 }
 
-size_t drift_smem_bytes(int M, int K, int T) {
-  return (size_t)M * T * drift_bin_bytes(K) + (size_t)kDrChunk * drift_stage_bytes(K);
+bool drift_fits(int M, int K, int T, int R, int smem_optin) {
+  return drift_smem_bytes(M, K, T, R) <= drift_dynamic_limit(smem_optin);
+}
+
+size_t drift_smem_bytes(int M, int K, int T, int R) {
+  return (size_t)R * M * T * drift_bin_bytes(K) + (size_t)kDrChunk * drift_stage_bytes(K);
 }
 
 int drift_max_basis() { return kDrMaxK; }
@@ -480,23 +663,24 @@ size_t drift_payload_bytes() { return sizeof(DriftObs); }
 
 cudaError_t drift_init_attributes(int max_smem) {
   const int lim = (int)drift_dynamic_limit(max_smem);
-  for (int K = 0; K <= kDrMaxK; ++K) {
-    const cudaError_t e = cudaFuncSetAttribute(drift_fn(K), cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-    if (e != cudaSuccess) return e;
-  }
+  for (int K = 0; K <= kDrMaxK; ++K)
+    for (int R = 1; R <= 2; ++R) {
+      const cudaError_t e = cudaFuncSetAttribute(drift_fn(K, R), cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+      if (e != cudaSuccess) return e;
+    }
   return cudaSuccess;
 }
 
-cudaError_t launch_drift(const DriftArgs& a, int T, cudaStream_t st) {
+cudaError_t launch_drift(const DriftArgs& a, int T, int R, cudaStream_t st) {
   if (a.ncurves <= 0) return cudaSuccess;
   drift_prep_kernel<<<(unsigned)a.ncurves, 256, 0, st>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || a.nfreq <= 0) return e;
-  const int64_t tiles = (a.nfreq + T - 1) / T;
+  const int64_t tiles = (a.nfreq + (int64_t)T * R - 1) / ((int64_t)T * R);
   if (a.timing_start) cudaEventRecord(a.timing_start, st);
   void* params[] = {const_cast<DriftArgs*>(&a)};
-  e = cudaLaunchKernel(drift_fn(a.K), dim3((unsigned)tiles, (unsigned)a.ncurves), dim3(T), params,
-                       drift_smem_bytes(a.M, a.K, T), st);
+  e = cudaLaunchKernel(drift_fn(a.K, R), dim3((unsigned)tiles, (unsigned)a.ncurves), dim3(T), params,
+                       drift_smem_bytes(a.M, a.K, T, R), st);
   if (e != cudaSuccess) return e;
   if (a.timing_stop) cudaEventRecord(a.timing_stop, st);
   if (a.k > 0) {

@@ -1142,8 +1142,18 @@ int fpw_periodogram_drift(fpw_ctx* ctx, void* stream, const fpw_params* params, 
   clear_stale_error();
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   ctx->last_stream = st;
-  const int T = drift_threads(M, K, ctx->smem_optin);
-  if (T == 0) return FPW_ENOTSUP;
+  // threads (32..128) and frequencies per thread (1 or 2) from params when
+  // set; by default the largest block with one frequency per thread, and two
+  // frequencies per thread for K <= 1 where they fit (8-byte bins: measured
+  // 16 % faster at K = 0; slower from K = 2 on, where 16-byte bins halve the
+  // resident warps)
+  if (p.threads != 0 && (p.threads % 32 != 0 || p.threads < 32 || p.threads > 128)) return FPW_ENOTSUP;
+  if (p.freqs_per_thread != 0 && p.freqs_per_thread != 1 && p.freqs_per_thread != 2) return FPW_ENOTSUP;
+  const int T = p.threads != 0 ? p.threads : drift_threads(M, K, ctx->smem_optin);
+  if (T == 0 || !drift_fits(M, K, T, 1, ctx->smem_optin)) return FPW_ENOTSUP;
+  int R = p.freqs_per_thread;
+  if (R == 0) R = (K <= 1 && drift_fits(M, K, T, 2, ctx->smem_optin)) ? 2 : 1;
+  if (!drift_fits(M, K, T, R, ctx->smem_optin)) return FPW_ENOTSUP;
   if (ncurves == 0) return FPW_OK;
   int64_t nobs = 0;
   FPW_CK(cudaMemcpyAsync(&nobs, offsets + ncurves, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
@@ -1196,7 +1206,7 @@ int fpw_periodogram_drift(fpw_ctx* ctx, void* stream, const fpw_params* params, 
     ctx->ev_used += 2;
   }
   FPW_CK(cudaMemsetAsync(words, 0, 2 * sizeof(unsigned), st));
-  FPW_CK(launch_drift(a, T, st));
+  FPW_CK(launch_drift(a, T, R, st));
   FPW_CK(launch_latch(words, st));
   return FPW_OK;
 }

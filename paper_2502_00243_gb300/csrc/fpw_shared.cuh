@@ -81,11 +81,12 @@ struct DriftArgs {
   cudaEvent_t timing_stop;
 };
 int drift_threads(int M, int K, int smem_optin);  // threads per block, 0 if M is too large
-size_t drift_smem_bytes(int M, int K, int T);
+size_t drift_smem_bytes(int M, int K, int T, int R);  // R frequencies per thread (1 or 2)
+bool drift_fits(int M, int K, int T, int R, int smem_optin);
 int drift_max_basis();
 size_t drift_payload_bytes();
 cudaError_t drift_init_attributes(int max_smem);
-cudaError_t launch_drift(const DriftArgs& a, int T, cudaStream_t st);
+cudaError_t launch_drift(const DriftArgs& a, int T, int R, cudaStream_t st);
 
 size_t shared_image_bytes(int64_t ncurves, int64_t n);
 int shared_curves_per_group();

@@ -205,3 +205,32 @@ def test_drift_strong_baseline(G, ctx, K, beta):
         assert_S_close(Sd[c], S_or, bound, absf=1e-9, mask=~near, what=f"K={K} drifting curve {c}")
         o_idx, o_S = oracle.topk(S_or, 7)
         check_topk(idx[c], Sk[c], o_idx, o_S, abs_tol=1e-9 * bound, o_dense=S_or, what=f"K={K} drifting curve {c}")
+
+
+@pytest.mark.parametrize("K,T,R", [(2, 64, 2), (3, 128, 2), (4, 32, 2), (3, 32, 1), (0, 128, 1), (1, 64, 2)])
+def test_drift_block_shapes(G, ctx, K, T, R):
+    """Every (threads, frequencies per thread) shape the drift call accepts,
+    against the dense oracle; a frequency count that leaves a partial tile."""
+    w = L.ragged(320 + K, [260, 33, 700], 611, M=14, k=4)
+    p = G.fpw_params_default(threads=T, freqs_per_thread=R, inv_alpha2=0.2)
+    idx, Sk, Sd, st = run_drift(G, ctx, w, 14, K, 0.8, 4, params=p)
+    assert st == 0
+    for c in range(w.ncurves):
+        t, x, s = w.curve(c)
+        S_or = oracle.fpw_drift(t, x, s, w.freqs, 14, K, 0.8, 0.2)
+        bound = s_bound(x, s)
+        near = oracle.min_edge(t, w.freqs, 14) <= 1e-9
+        assert_S_close(Sd[c], S_or, bound, mask=~near, what=f"K={K} T={T} R={R} curve {c}")
+        o_idx, o_S = oracle.topk(S_or, 8)
+        check_topk(idx[c], Sk[c], o_idx, o_S, abs_tol=1e-7 * bound, o_dense=S_or, what=f"K={K} T={T} R={R} curve {c}")
+
+
+def test_drift_rejects_unsupported_shapes(G, ctx):
+    """Valid parameters the drift kernel has no shape for give FPW_ENOTSUP;
+    invalid ones (48 threads) FPW_EINVAL, as for every call."""
+    w = L.ragged(330, [50], 64, M=8, k=2)
+    for kw, code in (({"threads": 256}, G.FPW_ENOTSUP), ({"freqs_per_thread": 4}, G.FPW_ENOTSUP),
+                     ({"threads": 48}, G.FPW_EINVAL)):
+        with pytest.raises(G.FPWError) as ei:
+            run_drift(G, ctx, w, 8, 2, 1.0, 2, params=G.fpw_params_default(**kw))
+        assert ei.value.code == code, kw
