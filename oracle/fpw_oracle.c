@@ -21,14 +21,14 @@
  *   Readings where the paper is silent (each also listed in the design doc):
  *     - the denominator is Eq. 1's B_m + 1/alpha^2 (not the appendix listing's
  *       factor-2 form); inv_alpha2 = 1/alpha^2 is a parameter (0 = the paper's
- *       "can be neglected" practice);
+ *       practice of neglecting the term);
  *     - a bin whose denominator is 0 (empty bin with inv_alpha2 = 0)
  *       contributes 0, the limit of A^2/(B + c) as c -> 0 with A = B = 0;
  *     - frac uses floor, so it is defined for negative t*f too;
  *     - M * phi can round up to M for phi just below 1: the bin is clamped to
  *       M - 1 (bins are half-open [m/M, (m+1)/M));
  *     - observations are accumulated in input order.
- *   Post-processing (Section 3.5, "highest amplitude peaks"): a peak is a
+ *   Post-processing (Section 3.5 reports the strongest peaks): a peak is a
  *   local maximum S_k > S_{k-1} and S_k >= S_{k+1} (one-sided at the grid
  *   ends); the k largest peaks by S, ties to the lower index, missing entries
  *   are index -1 and value NaN. A raw mode ranks every frequency.
