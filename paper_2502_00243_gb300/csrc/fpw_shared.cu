@@ -81,10 +81,12 @@ __host__ __device__ __forceinline__ uint32_t km_off(uint32_t r, uint32_t q, uint
 }
 
 // Approximate reciprocal (one special-function instruction, relative error
-// about 2^-23; subnormal results kept).
+// about 2^-23), subnormal inputs and results flushed to zero: the epilogue
+// drops denominators below FLT_MIN, and a reciprocal that flushes (a
+// denominator above 2^126) leaves a term far below the absolute tolerance.
 __device__ __forceinline__ float rcp_approx(float x) {
   float r;
-  asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
 
