@@ -44,6 +44,11 @@ MUTATIONS = {
     "shared_unweighted_numerator": ("A[bin[i]] += xc[i] * w;", "A[bin[i]] += xc[i];"),
     "edge_distance_drops_product_error": ("return fabs(r + (ue + (double)M * e)) / (double)M;",
                                           "return fabs(r + ue) / (double)M;"),
+    "entropy_base_two_log": ("      H -= p * log(p);", "      H -= p * log2(p);"),
+    "entropy_wrong_sign": ("      H -= p * log(p);", "      H += p * log(p);"),
+    "entropy_counts_not_normalised": ("double p = (double)cnt[m] / (double)n;", "double p = (double)cnt[m];"),
+    "entropy_counts_not_reset": ("    for (int m = 0; m < M; ++m) cnt[m] = 0;\n    for (int64_t i = 0; i < n; ++i) cnt[oracle_bin(t[i], freqs[k], M)] += 1;",
+                                 "    if (k == 0)\n      for (int m = 0; m < M; ++m) cnt[m] = 0;\n    for (int64_t i = 0; i < n; ++i) cnt[oracle_bin(t[i], freqs[k], M)] += 1;"),
 }
 
 
@@ -56,7 +61,16 @@ class Api:
         lib.oracle_bins.argtypes = [vp, i64, vp, i64, ci, vp, vp]
         lib.oracle_fpw_multi.argtypes = [vp, vp, vp, i64, vp, i64, ci, ci, d, vp]
         lib.oracle_fpw_shared.argtypes = [vp, i64, i64, vp, vp, vp, i64, ci, d, vp]
+        lib.oracle_phase_entropy.argtypes = [vp, i64, vp, i64, ci, vp]
         self.lib = lib
+
+    def phase_entropy(self, t, freqs, M):
+        t, freqs = np.ascontiguousarray(t, dtype=np.float64), np.ascontiguousarray(freqs, dtype=np.float64)
+        H = np.empty(freqs.shape[0])
+        rc = self.lib.oracle_phase_entropy(t.ctypes.data, t.shape[0], freqs.ctypes.data, freqs.shape[0], M,
+                                           H.ctypes.data)
+        assert rc == 0
+        return H
 
     def fpw_shared(self, t, x, sigma, freqs, M, c=0.0):
         t, x, sigma, freqs = (np.ascontiguousarray(a, dtype=np.float64) for a in (t, x, sigma, freqs))
@@ -171,6 +185,19 @@ def battery(api: Api) -> list[str]:
         b, _ = exact_bins(t, f, 3)
         if not all(np.isclose(S[c, q], dense_chi2_difference(x[c], sigma[c], b, 3, 1.0), rtol=1e-9) for c in range(3)):
             failed.append("shared")
+            break
+    # phase entropy: bin counts from exact phases, H = -sum (N_m/N) ln(N_m/N), at
+    # two frequencies in one call
+    rng = np.random.default_rng(22)
+    t = rng.uniform(0, 50, 13)
+    fs = np.array([0.83, 2.41])
+    H = api.phase_entropy(t, fs, 5)
+    for q, f in enumerate(fs):
+        b, _ = exact_bins(t, f, 5)
+        p = np.bincount(b, minlength=5) / t.size
+        p = p[p > 0]
+        if not np.isclose(H[q], float(-(p * np.log(p)).sum()), rtol=1e-12):
+            failed.append("entropy")
             break
     # top-k golden cases
     idx, _ = api.topk(np.array([1.0, 3.0, 2.0, 5.0, 5.0, 4.0, 6.0]), 3)
