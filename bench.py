@@ -234,7 +234,9 @@ def config_block(args, nbatches, batch_evals_mean):
             "curves_per_step": args.batch_curves, "nfreq": args.nfreq, "M": args.M, "k": args.k,
             "phase": "fixed64 (exact integer anchor + 64-bit stepping)", "bin_sums": "f32",
             "evals_per_step_mean": batch_evals_mean,
-            "l2": "inputs larger than L2 (>= 200 MB of float64 per batch, distinct batch each step)"}
+            "l2": (f"inputs larger than L2: {batch_evals_mean / args.nfreq * 24 / 1e6:.0f} MB of float64 t, x, sigma "
+                   f"per batch against 129 MB of L2, a distinct batch each step" if batch_evals_mean
+                   else "host run (no device caches)")}
 
 
 def oracle_rate(batch, ids, F_grid, M, k, nthreads):
