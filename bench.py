@@ -12,8 +12,10 @@ ten timed steps on one GPU cover the whole sweep once. Inputs are synthetic
 Reported: evaluations (observation x frequency pairs) per second for the whole
 job, the tile kernel's roofline fraction, an end-to-end number through the
 host-buffer C entry point, the FP64 CPU oracle on a bounded sample
-(cpu_baseline), and the plain binary64 one-curve-per-launch GPU form on a
-stratified curve sample.
+(cpu_baseline), the plain binary64 one-curve-per-launch GPU form and the
+batched call on the same stratified curve sample (their ratio is the speed-up),
+and, in `per_M`, the same sweep at the other bin counts of the throughput
+sweep (M = 10 and 50), each over one pass of the 1e5 curves.
 
 --impl reference times the FP64 CPU oracle instead (each step a bounded sample
 of the same workload).
@@ -41,12 +43,13 @@ NSM_NOMINAL = 152
 SM_MAX_MHZ_NOMINAL = 2070.0
 SMEM_EVALS_PER_CLK_SM = 8  # 16 B (A, B) read-modify-write per evaluation at 128 B/clk/SM
 KERNELS_PER_STEP = 5  # prep, tile_dev, tile, merge, latch
-# DRAM bytes (read + write) of one tile-kernel launch, from the ncu capture summarised in
-# profiles/tile_kernel_sweep_m20_m50_full.md (1e4 sweep curves, 2e4 frequencies): 143.2 MB. The kernel
-# reads each curve from DRAM once per launch (t and the staged weights, about 16.7 B per observation;
-# per-tile re-reads hit L2), so a full launch adds only the larger grid (8 B per extra frequency).
-# Valid only for the kernel source it was measured on (sha256 prefix of fpw_tile.cu + fpw_internal.cuh).
-TILE_TRAFFIC = {"source_sha256_16": "22ded89c0d53e517", "bytes": 143.55e6, "nfreq": 20_000}
+SWEEP_MS = (10, 20, 50)  # bin counts of the throughput sweep
+# DRAM bytes (read + write) of one tile-kernel launch at M = 20, from an ncu capture of a 1e4-curve sweep
+# batch over 2e4 frequencies (dram__bytes_read.sum + dram__bytes_write.sum). The kernel reads each curve
+# from DRAM once per launch (t and the staged weights, about 16.7 B per observation; per-tile re-reads
+# hit L2), so a full launch adds only the larger grid (8 B per extra frequency). Valid only for the
+# kernel source it was measured on (sha256 prefix of the tile-kernel sources, tile_source_hash).
+TILE_TRAFFIC = {"source_sha256_16": None, "bytes": None, "nfreq": 20_000}
 
 
 # ---------------------------------------------------------------- workload generation (spawned workers)
@@ -208,7 +211,7 @@ def sm_max_mhz():
 def tile_source_hash():
     import hashlib
     h = hashlib.sha256()
-    for f in ("fpw_tile.cu", "fpw_internal.cuh"):
+    for f in ("fpw_tile.cuh", "fpw_tile.cu", "fpw_tile_f32.cu", "fpw_internal.cuh"):
         with open(os.path.join(ROOT, "paper_2502_00243_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -217,7 +220,7 @@ def tile_source_hash():
 def tile_traffic(nfreq):
     """DRAM bytes per tile-kernel launch of the timed workload, or None when the
     kernel source changed since the counters were taken."""
-    if tile_source_hash() != TILE_TRAFFIC["source_sha256_16"]:
+    if TILE_TRAFFIC["bytes"] is None or tile_source_hash() != TILE_TRAFFIC["source_sha256_16"]:
         return None
     return TILE_TRAFFIC["bytes"] + 8.0 * (nfreq - TILE_TRAFFIC["nfreq"])
 
@@ -313,11 +316,15 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- GPU arm
+def shape_label(ctx, M):
+    T, R, NC, grid = ctx.last_shape()
+    return f"tile_kernel<R={R}, fixed64, f32 sums> T={T} obs_chunk={NC} grid={grid} (M={M})"
+
+
 def run_gb300(args):
     import numpy as np
     import torch
 
-    import lightcurves as L
     rank, world, local_rank = env_rank()
     dist = None
     if world > 1:
@@ -334,7 +341,10 @@ def run_gb300(args):
     nb = args.curves_total // args.batch_curves
     steps = args.warmup + args.steps
     batch_of = shard_batches(steps, world, rank, nb)
-    ids = sorted(set(batch_of))
+    other_Ms = [m for m in SWEEP_MS if m != args.M] if not args.no_per_m else []
+    pm_steps, pm_warm = min(args.steps, nb), min(args.warmup, 2)
+    pm_batch_of = shard_batches(pm_warm + pm_steps, world, rank, nb)
+    ids = sorted(set(batch_of) | (set(pm_batch_of) if other_Ms else set()))
     workers = max(1, min(16, cores // max(1, min(world, cores))))
     t_gen = time.perf_counter()
     host = make_batches(ids, args.batch_curves, args.M, workers=workers)
@@ -354,52 +364,62 @@ def run_gb300(args):
         tuned = autotune.tune(ctx, Ms=(args.M,))
     params = G.fpw_params_default()
     stream = torch.cuda.current_stream()
+    nsm = torch.cuda.get_device_properties(local_rank).multi_processor_count
+    peak = nsm * sm_max_mhz() * 1e6 * SMEM_EVALS_PER_CLK_SM / 1e9
 
-    def step(s):
-        b = batch_of[s]
+    def step(b, M):
         d = dev[b]
         G.fpw_periodogram_batch_ex(ctx, stream, params, d["offsets"], host[b][0], d["t"], d["x"], d["sigma"], freqs,
-                                   args.M, k, idx, Sk)
+                                   M, k, idx, Sk)
         return float(host[b][0][-1]) * F
 
-    for s in range(args.warmup):
-        step(s)
-    torch.cuda.synchronize()
-    if ctx.status() != 0:
-        raise RuntimeError("device status error during warm-up")
-    ctx.set_timing(True)
-    ctx.kernel_time()
-    clocks = ClockSampler(local_rank) if rank == 0 else None
-    if clocks:
-        clocks.start()
-        time.sleep(0.3)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    evals = 0.0
-    for s in range(args.warmup, steps):
-        evals += step(s)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    clk = clocks.stop() if clocks else None
-    ms = e0.elapsed_time(e1)
-    kern_ms, launches = ctx.kernel_time()
-    ctx.set_timing(False)
-    status = ctx.status()
-    if status != 0:
-        raise RuntimeError(f"device status {status} in the timed region")
-    ms_max, evals_all = reduce_timing(dist, "cuda", ms, evals)
-    value = evals_all / (ms_max / 1e3)
+    def timed_steps(M, order, warm):
+        """Warm-up, then the timed steps bracketed by barriers and device
+        syncs; CUDA events on the launching stream for the whole region and
+        (library hook) around each tile-kernel launch; clocks sampled during it."""
+        for b in order[:warm]:
+            step(b, M)
+        torch.cuda.synchronize()
+        if ctx.status() != 0:
+            raise RuntimeError("device status error during warm-up")
+        ctx.set_timing(True)
+        ctx.kernel_time()
+        clocks = ClockSampler(local_rank) if rank == 0 else None
+        if clocks:
+            clocks.start()
+            time.sleep(0.3)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        evals = 0.0
+        for b in order[warm:]:
+            evals += step(b, M)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        clk = clocks.stop() if clocks else None
+        ms = e0.elapsed_time(e1)
+        kern_ms, launches = ctx.kernel_time()
+        ctx.set_timing(False)
+        status = ctx.status()
+        if status != 0:
+            raise RuntimeError(f"device status {status} in the timed region")
+        ms_max, evals_all = reduce_timing(dist, "cuda", ms, evals)
+        return dict(ms=ms_max, evals_all=evals_all, evals=evals, kern_ms=kern_ms, launches=launches, clk=clk,
+                    label=shape_label(ctx, M))
+
+    head = timed_steps(args.M, batch_of, args.warmup)
+    value = head["evals_all"] / (head["ms"] / 1e3)
+    kern_ms, launches = head["kern_ms"], head["launches"]
 
     # ---- end to end through the host-buffer entry point (pinned host memory)
     e2e = None
     if not args.no_e2e:
         pinned = {}
-        for b in ids:
+        for b in sorted(set(batch_of)):
             arrs = []
             for a in host[b]:
                 p = torch.empty(a.shape, dtype=torch.from_numpy(a).dtype, pin_memory=True)
@@ -433,36 +453,59 @@ def run_gb300(args):
         e2e = {"value": ev_h / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d // args.steps),
                "d2h_bytes_per_step": int(d2h // args.steps), "api": "fpw_periodogram_batch_host"}
 
-    # ---- plain binary64 one-curve-per-launch GPU form, stratified sample
-    plain = None
-    if not args.no_plain:
-        b0 = ids[0]
+    # ---- the plain binary64 one-curve-per-launch GPU form and the batched call on the same curve sample
+    def plain_vs_batched(M):
+        b0 = batch_of[0]
         pick = stratified(host[b0][0], args.plain_curves)
         o, t, x, sg = subset(host[b0], pick)
         dp = [torch.from_numpy(a).cuda() for a in (o, t, x, sg)]
         pi = torch.empty(len(pick) * k, dtype=torch.int32, device="cuda")
         ps = torch.empty(len(pick) * k, dtype=torch.float32, device="cuda")
-        pp = G.fpw_params_default(phase_mode=G.FPW_PHASE_FP64)
-        G.fpw_periodogram_batch_ex(ctx, stream, pp, dp[0], o, dp[1], dp[2], dp[3], freqs, args.M, k, pi, ps)
-        torch.cuda.synchronize()
-        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        q0.record(stream)
-        G.fpw_periodogram_batch_ex(ctx, stream, pp, dp[0], o, dp[1], dp[2], dp[3], freqs, args.M, k, pi, ps)
-        q1.record(stream)
-        torch.cuda.synchronize()
-        pev = float(o[-1]) * F
-        pval = pev / (q0.elapsed_time(q1) / 1e3)
-        # the split-precision batched kernel on the same sample, for a like-for-like ratio
-        G.fpw_periodogram_batch_ex(ctx, stream, params, dp[0], o, dp[1], dp[2], dp[3], freqs, args.M, k, pi, ps)
-        torch.cuda.synchronize()
-        plain = {"value": pval, "unit": UNIT, "sample": f"{len(pick)} curves stratified by N from batch {b0}, "
-                 f"full grid, M={args.M}, one launch per curve (+1 top-k launch)",
-                 "speedup_of_batched_split": value / pval}
+
+        def rate(pp, reps):
+            G.fpw_periodogram_batch_ex(ctx, stream, pp, dp[0], o, dp[1], dp[2], dp[3], freqs, M, k, pi, ps)
+            torch.cuda.synchronize()
+            q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            q0.record(stream)
+            for _ in range(reps):
+                G.fpw_periodogram_batch_ex(ctx, stream, pp, dp[0], o, dp[1], dp[2], dp[3], freqs, M, k, pi, ps)
+            q1.record(stream)
+            torch.cuda.synchronize()
+            return reps * float(o[-1]) * F / (q0.elapsed_time(q1) / 1e3)
+
+        pval = rate(G.fpw_params_default(phase_mode=G.FPW_PHASE_FP64), 1)
+        bval = rate(params, 5)
+        return {"value": pval, "unit": UNIT, "sample": f"{len(pick)} curves stratified by N from batch {b0}, "
+                f"full grid, M={M}, one launch per curve (+1 top-k launch)", "batched_same_sample": bval,
+                "speedup_of_batched_split": bval / pval,
+                "speedup_vs_sweep_value": None}
+
+    plain = None
+    if not args.no_plain:
+        plain = plain_vs_batched(args.M)
+        plain["speedup_vs_sweep_value"] = value / plain["value"]
+
+    # ---- the other bin counts of the throughput sweep: one pass over the 1e5 curves each
+    per_M = {}
+    for M in other_Ms:
+        r = timed_steps(M, pm_batch_of, pm_warm)
+        v = r["evals_all"] / (r["ms"] / 1e3)
+        ach = r["evals"] / (r["kern_ms"] / 1e3) / 1e9 if r["kern_ms"] > 0 else None
+        ent = {"value": v, "unit": UNIT, "steps": pm_steps, "warmup": pm_warm,
+               "ms_per_step": r["ms"] / pm_steps, "kernel_ms_avg": r["kern_ms"] / max(r["launches"], 1),
+               "roofline_frac": (ach / peak) if ach else None, "achieved": ach, "peak": peak, "unit_roofline": "Geval/s",
+               "kernel": r["label"], "clocks": r["clk"]}
+        if not args.no_plain:
+            pv = plain_vs_batched(M)
+            ent["plain_fp64"] = pv["value"]
+            ent["batched_same_sample"] = pv["batched_same_sample"]
+            ent["speedup_of_batched_split"] = pv["speedup_of_batched_split"]
+        per_M[str(M)] = ent
 
     # ---- CPU oracle on a bounded sample (rank 0, one GPU only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        b0 = ids[0]
+        b0 = batch_of[0]
         pick, F_s = oracle_sample(host[b0], F_grid, args.M, k, args.cpu_seconds, cores)
         ev, dt = oracle_rate(host[b0], pick, F_s, args.M, k, cores)
         # one core: the sample's median-N curve over the first 2e5 grid frequencies (about 1 s)
@@ -478,23 +521,22 @@ def run_gb300(args):
                                      f"{min(200_000, F_s.shape[0])} of those frequencies, one thread"}
 
     if rank == 0:
-        nsm = torch.cuda.get_device_properties(local_rank).multi_processor_count
-        peak = nsm * sm_max_mhz() * 1e6 * SMEM_EVALS_PER_CLK_SM / 1e9
-        achieved = evals / (kern_ms / 1e3) / 1e9 if kern_ms > 0 else None
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Geval/s",
+        achieved = head["evals"] / (kern_ms / 1e3) / 1e9 if kern_ms > 0 else None
+        roof = {"bound": "smem", "achieved": achieved, "peak": peak, "unit": "Geval/s",
                 "frac": (achieved / peak) if achieved else None, "traffic": tile_traffic(F),
-                "kernel": "tile_kernel<R=4, fixed64, f32>", "launches": launches,
+                "kernel": head["label"], "launches": launches,
                 "kernel_ms_avg": kern_ms / max(launches, 1),
                 "peak_basis": f"shared-memory pipe: one 8 B load + one 8 B store of the (A,B) bin pair per "
                               f"evaluation at 128 B/clk/SM -> {SMEM_EVALS_PER_CLK_SM} evals/clk/SM x {nsm} SMs x "
-                              f"{sm_max_mhz():.0f} MHz (recipe unit counts and max clock)"}
-        mean_ev = float(np.mean([float(host[b][0][-1]) * F for b in ids]))
+                              f"{sm_max_mhz():.0f} MHz (recipe unit counts and max clock); the per-evaluation "
+                              f"instruction issue bound is higher"}
+        mean_ev = float(np.mean([float(host[b][0][-1]) * F for b in sorted(set(batch_of))]))
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "warmup": args.warmup, "ms_per_step": head["ms"] / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": config_block(args, nb, mean_ev), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": KERNELS_PER_STEP * args.steps, "clocks": clk, "plain_fp64": plain,
-                "gen_seconds": round(t_gen, 2), "autotuned": tuned}
+                "gpu_launches": KERNELS_PER_STEP * args.steps, "clocks": head["clk"], "plain_fp64": plain,
+                "per_M": per_M or None, "gen_seconds": round(t_gen, 2), "autotuned": tuned}
         print(json.dumps(line), flush=True)
     ctx.close()
     if dist:
@@ -840,6 +882,7 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-per-m", action="store_true", help="skip the M = 10 / 50 lines of the sweep")
     ap.add_argument("--autotune", action="store_true", help="measure and install tuned kernel shapes before timing")
     ap.add_argument("--configs", nargs="?", const="all", default=None,
                     choices=["all", "batch", "shared", "drift", "multi", "entropy"],

@@ -65,8 +65,11 @@ extern "C" {
                                binary64 bin sums, one launch per curve */
 #define FPW_PHASE_FP32 2    /* FP32 phase: anchor rounded to FP32 every K frequencies, FP32 steps */
 
-#define FPW_ACCUM_FP32 0 /* bin sums A_m, B_m in FP32 (default) */
-#define FPW_ACCUM_FP64 1 /* bin sums in binary64 */
+#define FPW_ACCUM_FP32 0      /* bin sums A_m, B_m in FP32 (default) */
+#define FPW_ACCUM_FP64 1      /* bin sums in binary64 */
+#define FPW_ACCUM_FP32_COMP 2 /* compensated FP32 bin sums: each term enters as an FP32 hi + lo pair and
+                                 every addition's rounding error is carried in a second FP32 sum
+                                 (about 48 significant bits; batched and single-curve calls) */
 
 #define FPW_PEAK_LOCALMAX 0 /* top-k over local maxima of S (default) */
 #define FPW_PEAK_RAW 1      /* top-k over every frequency */
@@ -249,6 +252,23 @@ FPW_API int fpw_periodogram_batch_host(fpw_ctx* ctx, const fpw_params* params, c
                                const double* t, const double* x, const double* sigma, const double* freqs,
                                int64_t nfreq, int M, int k, int32_t* topk_idx, float* topk_S);
 
+/* The batched call with a bin dump: runs exactly the kernels that
+ * fpw_periodogram_batch_ex runs for the same arguments and params (same kernel
+ * shape, tiles, phase anchors and stepping; params->use_graph is ignored), with
+ * no peaks, and additionally writes the phase bin (Appendix A.1, 0..M-1) that
+ * the periodogram kernel gave every observation at every frequency k with
+ * k0 <= k < k1, from the same arithmetic that forms the bin sums:
+ *   bins_out: device int32[(k1 - k0) * offsets[ncurves]], entry
+ *             [(k - k0) * offsets[ncurves] + i] for observation i (CSR index)
+ *   S_out:    optional device float64[ncurves * nfreq] dense periodograms
+ * Entries of curves with invalid data (status FPW_EDATA) are left unwritten.
+ * 0 <= k0 <= k1 <= nfreq. Other arguments as fpw_periodogram_batch_ex.
+ * Stream-ordered. Errors: FPW_EINVAL, FPW_ENOTSUP, FPW_ENOMEM, FPW_ECUDA. */
+FPW_API int fpw_periodogram_batch_bins(fpw_ctx* ctx, void* stream, const fpw_params* params, const int64_t* offsets,
+                                       const int64_t* offsets_host, int64_t ncurves, const double* t,
+                                       const double* x, const double* sigma, const double* freqs, int64_t nfreq,
+                                       int M, int64_t k0, int64_t k1, int32_t* bins_out, double* S_out);
+
 /* fpw_periodogram_batch without any device allocation. (The paper has no
  * counterpart: this is a deployment variant of the batched call.)
  * For callers that cannot call cudaMalloc: code that runs inside another
@@ -258,30 +278,23 @@ FPW_API int fpw_periodogram_batch_host(fpw_ctx* ctx, const fpw_params* params, c
  * file-scope device array of 32 MiB that every GPU loading the library holds
  * until the process exits; inputs and outputs are still the caller's.
  *   Arguments as fpw_periodogram_batch_ex (device pointers; offsets_host is an
- *   optional host copy of offsets, else offsets[ncurves] is read back), minus
- *   S_out. One work item per curve. phase_mode FPW_PHASE_FP64 is not supported.
- *   Limit: 64 + 16*C + 4*(C+1) + C + 12*C*k + 8*(nobs+2) bytes (16*(nobs+2)
- *   with FPW_ACCUM_FP64), each term rounded up to 256, must fit in 32 MiB
- *   (about 4 million observations); larger inputs return FPW_EINVAL.
+ *   optional host copy of offsets, else the offsets are read back to host
+ *   memory and checked there: offsets[0] = 0, non-decreasing, offsets[ncurves]
+ *   <= 2^40, FPW_EINVAL otherwise), minus S_out. One work item per curve,
+ *   largest curves first. phase_mode FPW_PHASE_FP64 is not supported.
+ *   Limit: 320 + 16*C + 4*(C+1) + C + 12*C*k + 8*(nobs+2) bytes (16*(nobs+2)
+ *   with FPW_ACCUM_FP64 or FPW_ACCUM_FP32_COMP), each term rounded up to 256,
+ *   must fit in 32 MiB (about 4 million observations); larger inputs return
+ *   FPW_EINVAL.
  *   The first call on a device (with that device current) looks up the
  *   array's device address; make it before any stream capture. Every call
  *   shares the array and clears what must start at zero; calls that overlap
  *   on the GPU race. Synchronizes `stream` before returning.
- * Errors: FPW_EINVAL, FPW_EDATA, FPW_ENOTSUP, FPW_ECUDA. */
+ * Errors: FPW_EINVAL, FPW_EDATA, FPW_ENOTSUP, FPW_ECUDA, FPW_ETIMEOUT. */
 FPW_API int fpw_periodogram_batch_noalloc(void* stream, const fpw_params* params, const int64_t* offsets,
                                           const int64_t* offsets_host, int64_t ncurves, const double* t,
                                           const double* x, const double* sigma, const double* freqs, int64_t nfreq,
                                           int M, int k, int32_t* topk_idx, float* topk_S);
-
-/* Diagnostic: the phase bin every observation gets at every frequency, computed
- * with the same device phase arithmetic as the periodogram kernels
- * (Appendix A.1 bin definition), for bin-mismatch accounting.
- *   t:        device float64[n];  freqs: device float64[nfreq]
- *   bins_out: device int32[nfreq * n], row per frequency
- * For FPW_PHASE_FIXED64 / FPW_PHASE_FP32 the anchors sit at frequency indices
- * that are multiples of params->K (FP32) or of the tile width (FIXED64). */
-FPW_API int fpw_debug_bins(fpw_ctx* ctx, void* stream, const fpw_params* params, const double* t, int64_t n,
-                   const double* freqs, int64_t nfreq, int M, int32_t* bins_out);
 
 /* Tuned kernel shapes. Adds a shape -- threads per block (multiple of 32,
  * 32..512), frequencies per thread (1, 2, 4 or 8) and observations per pass
@@ -295,6 +308,24 @@ FPW_API int fpw_ctx_set_shape(fpw_ctx* ctx, int M_lo, int M_hi, int64_t n_lo, in
                               int freqs_per_thread, int obs_chunk);
 FPW_API int fpw_ctx_clear_shapes(fpw_ctx* ctx);
 
+/* The tile-kernel shape of the context's most recent batched or single-curve
+ * call that ran the tile kernel: threads per block, frequencies per thread,
+ * observations staged per pass and the persistent grid (blocks). All zero
+ * before the first such call. Pass the first three as fpw_params threads /
+ * freqs_per_thread / obs_chunk to launch another call with the same tiles.
+ * Errors: FPW_EINVAL (null pointer). */
+FPW_API int fpw_ctx_last_shape(fpw_ctx* ctx, int* threads, int* freqs_per_thread, int* obs_chunk, int* grid);
+
+/* Limit, in SM clock cycles, of each wait inside the pipeline of the
+ * shared-timestamp kernel (fpw_periodogram_shared: its builder, copy and
+ * tensor-core roles wait on each other through mbarriers). 0 restores the
+ * default of 4e9 cycles (about 2 s). A wait that runs out makes the kernel
+ * stop its work, wait (with the default limit) for its own bulk copies and
+ * tensor-core operations in flight, free its tensor memory and return; the
+ * call's status is then FPW_ETIMEOUT (fpw_ctx_status), and the context stays
+ * usable. Errors: FPW_EINVAL (null ctx, clocks < 0). */
+FPW_API int fpw_ctx_set_wait_limit(fpw_ctx* ctx, int64_t clocks);
+
 /* Profiling hook. While enabled, the context records a pair of CUDA events on
  * the caller's stream around every launch of the periodogram kernel (the
  * persistent tile kernel; not in calls that use a CUDA graph).
@@ -307,7 +338,8 @@ FPW_API int fpw_ctx_kernel_time(fpw_ctx* ctx, double* ms, int64_t* launches);
 /* Human-readable text for a status code (static storage). */
 FPW_API const char* fpw_strerror(int status);
 
-/* Library ABI version (increments on incompatible changes). */
+/* Library ABI version (increments on incompatible changes; 2: fpw_debug_bins
+ * replaced by fpw_periodogram_batch_bins). */
 FPW_API int fpw_version(void);
 
 /* Text of the last CUDA runtime error seen by the calling thread (static,

@@ -22,14 +22,15 @@ LIB_PATH = os.path.join(HERE, "libfpw_gb300.so")
 
 FPW_OK, FPW_EINVAL, FPW_EDATA, FPW_ENOMEM, FPW_ECUDA, FPW_ETIMEOUT, FPW_ENOTSUP = range(7)
 FPW_PHASE_FIXED64, FPW_PHASE_FP64, FPW_PHASE_FP32 = 0, 1, 2
-FPW_ACCUM_FP32, FPW_ACCUM_FP64 = 0, 1
+FPW_ACCUM_FP32, FPW_ACCUM_FP64, FPW_ACCUM_FP32_COMP = 0, 1, 2
 FPW_PEAK_LOCALMAX, FPW_PEAK_RAW = 0, 1
 FPW_MAX_TOPK = 64
 
 EXPORTED = ("fpw_params_default", "fpw_ctx_create", "fpw_ctx_destroy", "fpw_ctx_status", "fpw_periodogram",
             "fpw_periodogram_ex", "fpw_periodogram_batch", "fpw_periodogram_batch_ex", "fpw_periodogram_batch_host",
-            "fpw_debug_bins", "fpw_strerror", "fpw_version", "fpw_last_cuda_error", "fpw_ctx_set_timing",
-            "fpw_ctx_kernel_time", "fpw_periodogram_batch_noalloc", "fpw_ctx_set_shape", "fpw_ctx_clear_shapes",
+            "fpw_periodogram_batch_bins", "fpw_ctx_last_shape", "fpw_ctx_set_wait_limit", "fpw_strerror",
+            "fpw_version", "fpw_last_cuda_error", "fpw_ctx_set_timing", "fpw_ctx_kernel_time",
+            "fpw_periodogram_batch_noalloc", "fpw_ctx_set_shape", "fpw_ctx_clear_shapes",
             "fpw_periodogram_batch_multi", "fpw_phase_entropy", "fpw_phase_entropy_peaks", "fpw_periodogram_shared",
             "fpw_periodogram_drift")
 
@@ -79,7 +80,9 @@ def lib():
                 "fpw_periodogram_batch": (ci, [vp, i64, vp, vp, vp, vp, i64, ci, ci, vp, vp]),
                 "fpw_periodogram_batch_ex": (ci, [vp, vp, P, vp, vp, i64, vp, vp, vp, vp, i64, ci, ci, vp, vp, vp]),
                 "fpw_periodogram_batch_host": (ci, [vp, P, vp, i64, vp, vp, vp, vp, i64, ci, ci, vp, vp]),
-                "fpw_debug_bins": (ci, [vp, vp, P, vp, i64, vp, i64, ci, vp]),
+                "fpw_periodogram_batch_bins": (ci, [vp, vp, P, vp, vp, i64, vp, vp, vp, vp, i64, ci, i64, i64, vp, vp]),
+                "fpw_ctx_last_shape": (ci, [vp] + [ctypes.POINTER(ci)] * 4),
+                "fpw_ctx_set_wait_limit": (ci, [vp, i64]),
                 "fpw_strerror": (ctypes.c_char_p, [ci]),
                 "fpw_version": (ci, []),
                 "fpw_last_cuda_error": (ctypes.c_char_p, []),
@@ -163,6 +166,16 @@ class Context:
 
     def set_timing(self, enable: bool) -> None:
         _check(lib().fpw_ctx_set_timing(self.handle, int(bool(enable))), "fpw_ctx_set_timing")
+
+    def set_wait_limit(self, clocks: int) -> None:
+        """Limit (SM clocks) of each wait in the shared-timestamp kernel's pipeline; 0 = default."""
+        _check(lib().fpw_ctx_set_wait_limit(self.handle, int(clocks)), "fpw_ctx_set_wait_limit")
+
+    def last_shape(self):
+        """(threads, freqs_per_thread, obs_chunk, grid) of the latest tile-kernel call."""
+        v = [ctypes.c_int() for _ in range(4)]
+        _check(lib().fpw_ctx_last_shape(self.handle, *[ctypes.byref(q) for q in v]), "fpw_ctx_last_shape")
+        return tuple(q.value for q in v)
 
     def kernel_time(self):
         """(milliseconds, launches) of the tile kernel since the last query."""
@@ -361,13 +374,26 @@ def fpw_periodogram_batch_host(ctx: Context, params, offsets, t, x, sigma, freqs
     return topk_idx, topk_S
 
 
-def fpw_debug_bins(ctx: Context, stream, params, t, freqs, M: int, bins_out):
+def fpw_periodogram_batch_bins(ctx: Context, stream, params, offsets, offsets_host, t, x, sigma, freqs, M: int,
+                               k0: int, k1: int, bins_out, S_out=None):
+    """The batched call's kernels with a bin dump: bins_out int32 ``[(k1 - k0) * nobs]``
+    receives the bin of every observation at frequencies k0 <= k < k1."""
     import torch
-    rc = lib().fpw_debug_bins(ctx.handle, _stream(stream), _params(params), _dev(t, torch.float64, "t"), t.numel(),
-                              _dev(freqs, torch.float64, "freqs"), freqs.numel(), int(M),
-                              _dev(bins_out, torch.int32, "bins_out"))
-    _check(rc, "fpw_debug_bins")
-    return bins_out
+    oh = None
+    if offsets_host is not None:
+        offsets_host = np.ascontiguousarray(offsets_host, dtype=np.int64)
+        oh = ctypes.c_void_p(offsets_host.ctypes.data)
+    rc = lib().fpw_periodogram_batch_bins(
+        ctx.handle, _stream(stream), _params(params), _dev(offsets, torch.int64, "offsets"), oh, offsets.numel() - 1,
+        _dev(t, torch.float64, "t"), _dev(x, torch.float64, "x"), _dev(sigma, torch.float64, "sigma"),
+        _dev(freqs, torch.float64, "freqs"), freqs.numel(), int(M), int(k0), int(k1),
+        _dev(bins_out, torch.int32, "bins_out"), _dev(S_out, torch.float64, "S_out") if S_out is not None else None)
+    _check(rc, "fpw_periodogram_batch_bins")
+    return bins_out, S_out
+
+
+def fpw_ctx_last_shape(ctx: Context):
+    return ctx.last_shape()
 
 
 def fpw_periodogram_batch_noalloc(stream, params, offsets, offsets_host, t, x, sigma, freqs, M: int, k: int, topk_idx,

@@ -5,8 +5,6 @@
 //   plain        the binary64 reference form: fl(t f) per evaluation, binary64
 //                bins (Appendix A.1) and sums (Eq. 1), one curve per launch
 //   dense_topk   top-k peaks of one dense periodogram (for the plain form)
-//   debug_bins   the bin each (frequency, observation) pair gets, with the same
-//                phase arithmetic as the tile kernel (mismatch accounting)
 #include <math.h>
 
 #include "fpw_internal.cuh"
@@ -35,8 +33,12 @@ __global__ void prep_kernel(const PrepArgs a) {
     const double w = ok ? 1.0 / (s * s) : 0.0;
     const double xa = ok ? x * w : 0.0;
     if (a.aw == nullptr) {
-    } else if (a.accum64) {
+    } else if (a.accum == FPW_ACCUM_FP64) {
       reinterpret_cast<double2*>(a.aw)[i] = make_double2(xa, w);
+    } else if (a.accum == FPW_ACCUM_FP32_COMP) {
+      // hi + lo FP32 pairs: the compensated sums add the low parts too
+      const float ah = (float)xa, wh = (float)w;
+      reinterpret_cast<float4*>(a.aw)[i] = make_float4(ah, wh, (float)(xa - (double)ah), (float)(w - (double)wh));
     } else {
       reinterpret_cast<float2*>(a.aw)[i] = make_float2((float)xa, (float)w);
     }
@@ -127,9 +129,11 @@ __global__ void merge_kernel(const MergeArgs a) {
 
 // Plain binary64 form. One thread per trial frequency; observations staged in
 // shared memory in chunks; per-thread bins [m][thread] as {A, B} binary64.
+// DUMP: also writes the bin of every (observation, frequency) in the window.
 constexpr int kPlainThreads = 128;
 constexpr int kPlainChunk = 256;
 
+template <bool DUMP>
 __global__ void __launch_bounds__(kPlainThreads) plain_kernel(const PlainArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   double* st = reinterpret_cast<double*>(smem);
@@ -159,6 +163,8 @@ __global__ void __launch_bounds__(kPlainThreads) plain_kernel(const PlainArgs a)
       const double ph = __dsub_rn(p, floor(p));
       int m = (int)floor(__dmul_rn((double)M, ph));
       m = m > M - 1 ? M - 1 : (m < 0 ? 0 : m);
+      if (DUMP && k < a.nfreq && k >= a.bins_k0 && k < a.bins_k1)
+        a.bins_out[(k - a.bins_k0) * a.bins_nobs + a.bins_base + o + i] = m;
       double2* b = &bins[m * kPlainThreads + tid];
       double2 v = *b;
       v.x = __dadd_rn(v.x, sa[i]);
@@ -247,49 +253,6 @@ __global__ void __launch_bounds__(kTopkThreads) dense_topk_kernel(const DenseTop
   }
 }
 
-// Bins as the periodogram kernels assign them. FIXED64 / FP32: anchor at the
-// nearest lower multiple of anchor_every; grid spacing df from the end points;
-// pairs whose grid deviates from linear by more than kGridTolCycles use the
-// exact per-frequency phase (as the tile kernel's fallback does).
-__global__ void debug_bins_kernel(const DebugBinsArgs a) {
-  const int64_t total = a.nfreq * a.n;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t F = a.nfreq;
-  const double df = (F > 1) ? (a.freqs[F - 1] - a.freqs[0]) / (double)(F - 1) : 0.0;
-  const unsigned M = (unsigned)a.M;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
-    const int64_t k = e / a.n, i = e % a.n;
-    const double t = a.t[i], f = a.freqs[k];
-    unsigned m;
-    if (a.phase_mode == FPW_PHASE_FP64) {
-      const double p = __dmul_rn(t, f);
-      const double ph = __dsub_rn(p, floor(p));
-      int mm = (int)floor(__dmul_rn((double)a.M, ph));
-      m = (unsigned)(mm > a.M - 1 ? a.M - 1 : (mm < 0 ? 0 : mm));
-    } else {
-      const int64_t ak = k - (k % a.anchor_every);
-      const double fa = a.freqs[ak];
-      const double pred = fma((double)(k - ak), df, fa);
-      if (fabs(f - pred) * fabs(t) > kGridTolCycles) {
-        m = bin_of_phase(phase_fixed64(t, f), M);
-      } else {
-        const unsigned long long P = phase_fixed64(t, fa), D = phase_fixed64(t, df);
-        if (a.phase_mode == FPW_PHASE_FIXED64) {
-          m = bin_of_phase(P + (unsigned long long)(k - ak) * D, M);
-        } else {
-          const float d32 = (float)(unsigned)(D >> 32) * 0x1p-32f;
-          const float p32 = (float)(unsigned)(P >> 32) * 0x1p-32f;
-          float p = fmaf((float)(k - ak), d32, p32);
-          p = p - floorf(p);
-          m = (unsigned)(p * (float)a.M);
-          m = m < M ? m : M - 1u;
-        }
-      }
-    }
-    a.bins[e] = (int32_t)m;
-  }
-}
-
 __global__ void latch_kernel(unsigned* words) { words[2] |= words[1]; }
 
 __global__ void fill_topk_kernel(int32_t* idx, float* S, int64_t n) {
@@ -333,29 +296,25 @@ cudaError_t launch_merge(const MergeArgs& a, cudaStream_t st) {
 size_t plain_smem_bytes(int M) { return (size_t)3 * kPlainChunk * 8 + (size_t)M * kPlainThreads * 16; }
 
 cudaError_t plain_init_attributes(int max_smem) {
-  return cudaFuncSetAttribute(plain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+  cudaError_t e = cudaFuncSetAttribute(plain_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(plain_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
 }
 
 cudaError_t launch_plain(const PlainArgs& a, cudaStream_t st) {
   if (a.nfreq <= 0) return cudaSuccess;
   const size_t smem = plain_smem_bytes(a.M);
   const int64_t blocks = (a.nfreq + kPlainThreads - 1) / kPlainThreads;
-  plain_kernel<<<(unsigned)blocks, kPlainThreads, smem, st>>>(a);
+  if (a.bins_out)
+    plain_kernel<true><<<(unsigned)blocks, kPlainThreads, smem, st>>>(a);
+  else
+    plain_kernel<false><<<(unsigned)blocks, kPlainThreads, smem, st>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_dense_topk(const DenseTopkArgs& a, cudaStream_t st) {
   if (a.k <= 0) return cudaSuccess;
   dense_topk_kernel<<<1, kTopkThreads, 0, st>>>(a);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_debug_bins(const DebugBinsArgs& a, cudaStream_t st) {
-  const int64_t total = a.nfreq * a.n;
-  if (total <= 0) return cudaSuccess;
-  int64_t blocks = (total + 255) / 256;
-  blocks = blocks > 65535 ? 65535 : blocks;
-  debug_bins_kernel<<<(unsigned)blocks, 256, 0, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -35,7 +35,8 @@ struct TileArgs {
   const double* t;           // observation times, CSR by curve
   const int64_t* offsets;    // [ncurves + 1]; NULL: one curve of n_single observations
   int64_t n_single;
-  const void* aw;            // prep output: float2 or double2 {a = x w, w = 1/sigma^2} per observation
+  const void* aw;            // prep output per observation: float2 {a = x w, w = 1/sigma^2}, double2, or
+                             // float4 {a_hi, w_hi, a_lo, w_lo} (compensated sums)
   const double* freqs;       // [nfreq]
   int64_t nfreq;
   const WorkItem* items;     // [nitems], cost-descending
@@ -56,6 +57,8 @@ struct TileArgs {
   int ngroups;               // several-M kernel: number of groups (0 = the single-M kernel)
   int group_g[kMaxGroups];   // M = M / group_g[q] for group q
   int64_t group_rows;        // candidate rows per group (cand tables are [group][slot][k])
+  int32_t* bins_out;         // NULL, or bins of (k, i) for bins_k0 <= k < bins_k1 at [(k - bins_k0) * bins_nobs + i]
+  int64_t bins_k0, bins_k1, bins_nobs;
 };
 
 struct PrepArgs {
@@ -67,8 +70,8 @@ struct PrepArgs {
   int64_t nobs;
   const double* freqs;
   int64_t nfreq;
-  void* aw;                // float2 or double2 [nobs]
-  int accum64;
+  void* aw;                // [nobs] float2, double2 or float4 (see TileArgs::aw), or NULL
+  int accum;               // FPW_ACCUM_*
   uint8_t* curve_bad;      // [ncurves], zeroed before launch
   unsigned* status;
 };
@@ -98,6 +101,9 @@ struct PlainArgs {           // binary64 plain form, one curve
   double inv_alpha2;
   double* S_out;             // [nfreq]
   unsigned* status;
+  int32_t* bins_out;         // NULL, or bins of (k, i) for bins_k0 <= k < bins_k1 at
+  int64_t bins_k0, bins_k1;  //   [(k - bins_k0) * bins_nobs + bins_base + i]
+  int64_t bins_nobs, bins_base;
 };
 
 struct DenseTopkArgs {       // top-k of one dense periodogram (plain form)
@@ -110,16 +116,9 @@ struct DenseTopkArgs {       // top-k of one dense periodogram (plain form)
   const unsigned* status;
 };
 
-struct DebugBinsArgs {
-  const double* t;
-  int64_t n;
-  const double* freqs;
-  int64_t nfreq;
-  int M;
-  int phase_mode;
-  int anchor_every;          // anchor spacing in frequency indices
-  int32_t* bins;             // [nfreq * n]
-};
+// Bytes of one tile-kernel bin (A, B [, cA, cB]) and of one staged weight
+// record per accumulation mode (FPW_ACCUM_*).
+__host__ __device__ constexpr size_t accum_bin_bytes(int accum) { return accum == FPW_ACCUM_FP32 ? 8 : 16; }
 
 // Tile-kernel shape chosen by the host (tuned per bin count and curve size).
 struct TileShape {
@@ -130,18 +129,19 @@ struct TileShape {
 };
 
 // ---- launch wrappers (defined in the .cu files) -------------------------
-size_t tile_smem_bytes(int T, int R, int M, int NC, int k, bool accum64, int ngroups = 0);
-int tile_max_blocks_per_sm(int R, int phase_mode, bool accum64, int T, size_t smem, bool multi = false);
+size_t tile_smem_bytes(int T, int R, int M, int NC, int k, int accum, int ngroups = 0);
+int tile_max_blocks_per_sm(int R, int phase_mode, int accum, int T, size_t smem, bool multi = false,
+                           bool dump = false);
 bool tile_supported_R(int R);
-cudaError_t launch_tile(const TileArgs& a, const TileShape& s, int phase_mode, bool accum64, int grid,
-                        cudaStream_t st);
+// Launches the kernel for (R, phase, accum); several-M when a.ngroups > 0, the
+// bin-dumping instantiation when a.bins_out != NULL.
+cudaError_t launch_tile(const TileArgs& a, const TileShape& s, int phase_mode, int accum, int grid, cudaStream_t st);
 cudaError_t launch_prep(const PrepArgs& a, cudaStream_t st);
 // Per-tile grid deviation for tiles of width W starting at q*(W-2)-1, q < tiles.
 cudaError_t launch_tile_dev(const double* freqs, int64_t F, int W, int64_t tiles, double* dev, cudaStream_t st);
 cudaError_t launch_merge(const MergeArgs& a, cudaStream_t st);
 cudaError_t launch_plain(const PlainArgs& a, cudaStream_t st);
 cudaError_t launch_dense_topk(const DenseTopkArgs& a, cudaStream_t st);
-cudaError_t launch_debug_bins(const DebugBinsArgs& a, cudaStream_t st);
 cudaError_t launch_latch(unsigned* words, cudaStream_t st);  // words[2] |= words[1]
 cudaError_t launch_fill_topk(int32_t* idx, float* S, int64_t n, cudaStream_t st);
 cudaError_t tile_init_attributes(int max_smem);

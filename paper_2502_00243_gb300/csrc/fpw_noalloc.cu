@@ -41,18 +41,54 @@ struct DeviceSetup {
 std::mutex g_setup_mu;
 DeviceSetup g_setup[64];
 
-__global__ void noalloc_items_kernel(WorkItem* items, int32_t* cand_base, int64_t C, int64_t F) {
+// Work list: one item per curve, ordered by decreasing size class (a counting
+// sort on floor(log2 n) + 1 in the scratch array), so that the persistent
+// kernel starts the longest curves first. Within a class the order is
+// whatever the atomics give; it changes no result, only the schedule.
+constexpr int kSizeClasses = 64;
+
+__device__ __forceinline__ int size_class(const int64_t* offsets, int64_t c) {
+  const int64_t n = offsets[c + 1] - offsets[c];
+  return n > 0 ? __clzll((long long)n) : 63;  // larger n, smaller class
+}
+
+__global__ void noalloc_count_kernel(const int64_t* offsets, int64_t C, unsigned* hist, int32_t* cand_base) {
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c <= C; c += (int64_t)gridDim.x * blockDim.x) {
     cand_base[c] = (int32_t)c;
-    if (c < C) {
-      WorkItem w;
-      w.curve = (int32_t)c;
-      w.f_lo = 0;
-      w.f_hi = (int32_t)F;
-      w.slot = (int32_t)c;
-      items[c] = w;
-    }
+    if (c < C) atomicAdd(&hist[size_class(offsets, c)], 1u);
   }
+}
+
+__global__ void noalloc_scan_kernel(unsigned* hist) {  // one thread: exclusive prefix sums, in place
+  unsigned run = 0;
+  for (int q = 0; q < kSizeClasses; ++q) {
+    const unsigned h = hist[q];
+    hist[q] = run;
+    run += h;
+  }
+}
+
+__global__ void noalloc_items_kernel(const int64_t* offsets, int64_t C, int64_t F, unsigned* cursor, WorkItem* items) {
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < C; c += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned pos = atomicAdd(&cursor[size_class(offsets, c)], 1u);
+    WorkItem w;
+    w.curve = (int32_t)c;
+    w.f_lo = 0;
+    w.f_hi = (int32_t)F;
+    w.slot = (int32_t)c;
+    items[pos] = w;
+  }
+}
+
+// offsets[0] = 0, non-decreasing, total <= 2^40; `prev` carries the last
+// offset of the previous chunk (-1 for the first).
+bool offsets_chunk_ok(const int64_t* o, int64_t cnt, int64_t& prev) {
+  for (int64_t q = 0; q < cnt; ++q) {
+    if (prev < 0 ? o[q] != 0 : o[q] < prev) return false;
+    if (o[q] > ((int64_t)1 << 40)) return false;
+    prev = o[q];
+  }
+  return true;
 }
 
 int setup_device(int dev, DeviceSetup** out) {
@@ -96,7 +132,7 @@ extern "C" FPW_API int fpw_periodogram_batch_noalloc(void* stream, const fpw_par
   if (params) p = *params;
   if (!(p.inv_alpha2 >= 0.0) || p.inv_alpha2 > 1e300 || p.K < 1) return FPW_EINVAL;
   if (p.phase_mode != FPW_PHASE_FIXED64 && p.phase_mode != FPW_PHASE_FP32) return FPW_ENOTSUP;
-  if (p.accum != FPW_ACCUM_FP32 && p.accum != FPW_ACCUM_FP64) return FPW_EINVAL;
+  if (p.accum != FPW_ACCUM_FP32 && p.accum != FPW_ACCUM_FP64 && p.accum != FPW_ACCUM_FP32_COMP) return FPW_EINVAL;
   if (p.threads != 0 && (p.threads < 32 || p.threads > 512 || p.threads % 32 != 0)) return FPW_EINVAL;
   if (p.freqs_per_thread != 0 && !tile_supported_R(p.freqs_per_thread)) return FPW_EINVAL;
   if (p.obs_chunk != 0 && p.obs_chunk < 32) return FPW_EINVAL;
@@ -109,31 +145,36 @@ extern "C" FPW_API int fpw_periodogram_batch_noalloc(void* stream, const fpw_par
   if (rc != FPW_OK) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
 
-  // number of observations: from the host copy, else 8 bytes read back
-  int64_t nobs = 0;
+  // Every offset is checked before a kernel indexes the observations with it:
+  // the host copy when given, else the device offsets read back through a
+  // fixed buffer on the stack (no allocation).
+  int64_t nobs = 0, prev = -1;
   if (offsets_host) {
-    if (offsets_host[0] != 0) return FPW_EINVAL;
-    for (int64_t c = 0; c < ncurves; ++c)
-      if (offsets_host[c + 1] < offsets_host[c]) return FPW_EINVAL;
-    nobs = offsets_host[ncurves];
+    if (!offsets_chunk_ok(offsets_host, ncurves + 1, prev)) return FPW_EINVAL;
   } else {
-    if (cudaMemcpyAsync(&nobs, offsets + ncurves, sizeof(int64_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaStreamSynchronize(st) != cudaSuccess)
-      return FPW_ECUDA;
-    if (nobs < 0) return FPW_EINVAL;
+    constexpr int64_t kChunk = 2048;
+    int64_t buf[kChunk];
+    for (int64_t q = 0; q <= ncurves; q += kChunk) {
+      const int64_t cnt = (ncurves + 1 - q) < kChunk ? (ncurves + 1 - q) : kChunk;
+      if (cudaMemcpyAsync(buf, offsets + q, sizeof(int64_t) * (size_t)cnt, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+          cudaStreamSynchronize(st) != cudaSuccess)
+        return FPW_ECUDA;
+      if (!offsets_chunk_ok(buf, cnt, prev)) return FPW_EINVAL;
+    }
   }
+  nobs = prev;
   if (nobs > 0 && (!t || !x || !sigma)) return FPW_EINVAL;
 
   // kernel shape: as the tuned default, with the chunk sized to fit two blocks per SM
-  const bool acc64 = p.accum == FPW_ACCUM_FP64;
+  const bool wide = p.accum != FPW_ACCUM_FP32;  // 16-byte bins
   TileShape sh{};
   sh.threads = p.threads ? p.threads : 128;
-  sh.R = p.freqs_per_thread ? p.freqs_per_thread : (acc64 ? 2 : (M <= 24 ? 4 : 2));
+  sh.R = p.freqs_per_thread ? p.freqs_per_thread : (wide ? 2 : (M <= 24 ? 4 : 2));
   int NC = p.obs_chunk;
   if (!NC) {
     for (int blocks : {2, 1}) {
       for (int nc = 4096; nc >= 32; nc -= 32) {
-        const size_t s = tile_smem_bytes(sh.threads, sh.R, M, nc, k, acc64);
+        const size_t s = tile_smem_bytes(sh.threads, sh.R, M, nc, k, p.accum);
         if (s <= (size_t)ds->smem_optin && (s + 1024) * blocks <= (size_t)ds->smem_per_sm) {
           NC = nc;
           break;
@@ -145,23 +186,25 @@ extern "C" FPW_API int fpw_periodogram_batch_noalloc(void* stream, const fpw_par
     if (!NC) return FPW_ENOTSUP;
   }
   sh.obs_chunk = NC;
-  sh.smem = tile_smem_bytes(sh.threads, sh.R, M, NC, k, acc64);
+  sh.smem = tile_smem_bytes(sh.threads, sh.R, M, NC, k, p.accum);
   if (sh.smem > (size_t)ds->smem_optin) return FPW_ENOTSUP;
-  const int bps = tile_max_blocks_per_sm(sh.R, p.phase_mode, acc64, sh.threads, sh.smem);
+  const int bps = tile_max_blocks_per_sm(sh.R, p.phase_mode, p.accum, sh.threads, sh.smem);
   if (bps < 1) return FPW_ENOTSUP;
 
   // scratch layout (256-byte aligned sections); reject inputs that do not fit
-  const size_t o_words = 0;
-  const size_t o_items = up256(o_words + 64);
+  const size_t o_words = 0;  // counter, status (64 B), then the size-class histogram
+  const size_t o_hist = o_words + 64;
+  const size_t o_items = up256(o_hist + kSizeClasses * sizeof(unsigned));
   const size_t o_base = up256(o_items + (size_t)ncurves * sizeof(WorkItem));
   const size_t o_bad = up256(o_base + (size_t)(ncurves + 1) * sizeof(int32_t));
   const size_t o_cS = up256(o_bad + (size_t)ncurves);
   const size_t o_cI = up256(o_cS + (size_t)ncurves * k * sizeof(double));
   const size_t o_aw = up256(o_cI + (size_t)ncurves * k * sizeof(int32_t));
-  const size_t end = o_aw + (size_t)(nobs + 2) * (acc64 ? 16 : 8);
+  const size_t end = o_aw + (size_t)(nobs + 2) * accum_bin_bytes(p.accum);
   if (end > kScratchBytes) return FPW_EINVAL;
   unsigned char* S = ds->scratch;
   unsigned* words = reinterpret_cast<unsigned*>(S + o_words);
+  unsigned* hist = reinterpret_cast<unsigned*>(S + o_hist);
   WorkItem* items = reinterpret_cast<WorkItem*>(S + o_items);
   int32_t* cand_base = reinterpret_cast<int32_t*>(S + o_base);
   uint8_t* curve_bad = S + o_bad;
@@ -169,14 +212,16 @@ extern "C" FPW_API int fpw_periodogram_batch_noalloc(void* stream, const fpw_par
   int32_t* cand_idx = reinterpret_cast<int32_t*>(S + o_cI);
   void* aw = S + o_aw;
 
-  // counter, call status and per-curve flags must start at zero: the array
-  // keeps whatever the previous call left in it
-  if (cudaMemsetAsync(words, 0, 64, st) != cudaSuccess) return FPW_ECUDA;
+  // counter, call status, histogram and per-curve flags must start at zero:
+  // the array keeps whatever the previous call left in it
+  if (cudaMemsetAsync(words, 0, o_items - o_words, st) != cudaSuccess) return FPW_ECUDA;
   if (cudaMemsetAsync(curve_bad, 0, (size_t)ncurves, st) != cudaSuccess) return FPW_ECUDA;
   {
     int64_t blocks = (ncurves + 1 + 255) / 256;
     blocks = blocks > 4096 ? 4096 : blocks;
-    noalloc_items_kernel<<<(unsigned)blocks, 256, 0, st>>>(items, cand_base, ncurves, nfreq);
+    noalloc_count_kernel<<<(unsigned)blocks, 256, 0, st>>>(offsets, ncurves, hist, cand_base);
+    noalloc_scan_kernel<<<1, 1, 0, st>>>(hist);
+    noalloc_items_kernel<<<(unsigned)blocks, 256, 0, st>>>(offsets, ncurves, nfreq, hist, items);
     if (cudaGetLastError() != cudaSuccess) return FPW_ECUDA;
   }
   PrepArgs pa{};
@@ -189,7 +234,7 @@ extern "C" FPW_API int fpw_periodogram_batch_noalloc(void* stream, const fpw_par
   pa.freqs = freqs;
   pa.nfreq = nfreq;
   pa.aw = aw;
-  pa.accum64 = acc64 ? 1 : 0;
+  pa.accum = p.accum;
   pa.curve_bad = curve_bad;
   pa.status = words + 1;
   if (launch_prep(pa, st) != cudaSuccess) return FPW_ECUDA;
@@ -216,7 +261,7 @@ extern "C" FPW_API int fpw_periodogram_batch_noalloc(void* stream, const fpw_par
   ta.inv_alpha2 = p.inv_alpha2;
   int grid = bps * ds->nsm;
   grid = grid < (int)ncurves ? grid : (int)ncurves;
-  if (launch_tile(ta, sh, p.phase_mode, acc64, grid, st) != cudaSuccess) return FPW_ECUDA;
+  if (launch_tile(ta, sh, p.phase_mode, p.accum, grid, st) != cudaSuccess) return FPW_ECUDA;
   if (k > 0) {
     MergeArgs ma{};
     ma.cand_S = cand_S;

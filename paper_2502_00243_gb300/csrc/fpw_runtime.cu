@@ -92,6 +92,7 @@ struct Plan {
   int nitems = 0;
   int nslots = 0;
   DevBuf items, cand_base;
+  void* host_stage = nullptr;  // pinned copy of items + cand_base, the source of the asynchronous upload
   uint64_t use = 0;
 };
 
@@ -134,6 +135,9 @@ struct fpw_ctx {
   bool timing = false;
   std::vector<cudaEvent_t> ev;  // pairs (start, stop) of recorded tile launches
   size_t ev_used = 0;           // events in use (even count)
+  TileShape last_shape{};       // shape and grid of the latest tile-kernel call
+  int last_grid = 0;
+  long long wait_clocks = 0;    // shared-timestamp pipeline wait limit (0: default)
 };
 
 namespace {
@@ -142,6 +146,14 @@ void free_buf(DevBuf& b) {
   if (b.p) cudaFree(b.p);
   b.p = nullptr;
   b.cap = 0;
+}
+
+// Frees a plan; cudaFree synchronizes the device first, so its upload has ended.
+void free_plan(Plan* p) {
+  free_buf(p->items);
+  free_buf(p->cand_base);
+  if (p->host_stage) cudaFreeHost(p->host_stage);
+  delete p;
 }
 
 // Discard a stale error left by an earlier, unrelated runtime call so that the
@@ -158,7 +170,7 @@ bool valid_params(const fpw_params& p) {
   if (!(p.inv_alpha2 >= 0.0) || !std::isfinite(p.inv_alpha2)) return false;
   if (p.phase_mode != FPW_PHASE_FIXED64 && p.phase_mode != FPW_PHASE_FP64 && p.phase_mode != FPW_PHASE_FP32)
     return false;
-  if (p.accum != FPW_ACCUM_FP32 && p.accum != FPW_ACCUM_FP64) return false;
+  if (p.accum != FPW_ACCUM_FP32 && p.accum != FPW_ACCUM_FP64 && p.accum != FPW_ACCUM_FP32_COMP) return false;
   if (p.K < 1) return false;
   if (p.peak_mode != FPW_PEAK_LOCALMAX && p.peak_mode != FPW_PEAK_RAW) return false;
   if (p.threads != 0 && (p.threads < 32 || p.threads > 512 || p.threads % 32 != 0)) return false;
@@ -168,8 +180,8 @@ bool valid_params(const fpw_params& p) {
 }
 
 // Kernel shape: T threads, R frequencies per thread, NC observations per pass.
-// Per-thread bins take R*M*T*(8|16) bytes; the observation chunk takes
-// NC*(16 + 8|16) bytes. Precedence: explicit params > the context's tuned
+// Per-thread bins take R*M*T*(8|16) bytes (16 for binary64 and compensated
+// sums); the observation chunk takes NC*(16 + 8|16) bytes. Precedence: explicit params > the context's tuned
 // table (fpw_ctx_set_shape) > the built-in defaults, which were measured on a
 // GB300 with ZTF-like curves (threads x frequencies-per-thread sweeps at
 // M = 10, 20, 50): R = 8 for M <= 12, R = 4 for M <= 24 (R = 2 when the
@@ -179,9 +191,9 @@ bool valid_params(const fpw_params& p) {
 // accumulates), else one block per SM.
 int choose_shape(fpw_ctx* ctx, const fpw_params& p, int M, int k, int64_t max_n, int64_t n_typ, int ngroups,
                  TileShape& out) {
-  const bool acc64 = p.accum == FPW_ACCUM_FP64;
+  const bool wide = p.accum != FPW_ACCUM_FP32;  // 16-byte bins
   int T = 128, R = 4, NC = 0;
-  if (acc64)
+  if (wide)
     R = 2;
   else if (M <= 12)
     R = 8;
@@ -207,11 +219,11 @@ int choose_shape(fpw_ctx* ctx, const fpw_params& p, int M, int k, int64_t max_n,
   if (p.freqs_per_thread) R = p.freqs_per_thread;
   if (p.obs_chunk) NC = p.obs_chunk;
   const bool fixedT = p.threads != 0;
-  while (!fixedT && T > 32 && tile_smem_bytes(T, R, M, 32, k, acc64, ngroups) > (size_t)ctx->smem_optin) T /= 2;
+  while (!fixedT && T > 32 && tile_smem_bytes(T, R, M, 32, k, p.accum, ngroups) > (size_t)ctx->smem_optin) T /= 2;
   const int64_t want_nc = std::max<int64_t>(32, ((max_n + 31) / 32) * 32);
   const size_t per_sm = (size_t)ctx->smem_per_sm;
   auto fits = [&](int blocks, int nc) {
-    const size_t s = tile_smem_bytes(T, R, M, nc, k, acc64, ngroups);
+    const size_t s = tile_smem_bytes(T, R, M, nc, k, p.accum, ngroups);
     return s <= (size_t)ctx->smem_optin && (s + 1024) * blocks <= per_sm;
   };
   if (!NC) {
@@ -233,7 +245,7 @@ int choose_shape(fpw_ctx* ctx, const fpw_params& p, int M, int k, int64_t max_n,
     }
     if (!NC) return FPW_ENOTSUP;  // the bins alone exceed shared memory
   }
-  const size_t smem = tile_smem_bytes(T, R, M, NC, k, acc64, ngroups);
+  const size_t smem = tile_smem_bytes(T, R, M, NC, k, p.accum, ngroups);
   if (smem > (size_t)ctx->smem_optin) return FPW_ENOTSUP;
   out.threads = T;
   out.R = R;
@@ -245,9 +257,9 @@ int choose_shape(fpw_ctx* ctx, const fpw_params& p, int M, int k, int64_t max_n,
 // Work items: each curve's frequency range split into segments of whole tiles
 // so that every resident block gets several items (load balance), sorted by
 // cost (observations x frequencies) descending; candidate rows per curve in
-// curve order.
+// curve order. The tables are uploaded from a pinned copy, ordered on `st`.
 Plan* build_plan(fpw_ctx* ctx, const int64_t* off, int64_t C, int64_t F, const TileShape& sh, int blocks_per_sm,
-                 uint64_t key, int* err) {
+                 uint64_t key, cudaStream_t st, int* err) {
   *err = FPW_OK;
   const int64_t Wown = (int64_t)sh.threads * sh.R - 2;
   const int64_t tiles = (F + Wown - 1) / Wown;
@@ -291,24 +303,27 @@ Plan* build_plan(fpw_ctx* ctx, const int64_t* off, int64_t C, int64_t F, const T
   pl->nitems = (int)sorted.size();
   pl->nslots = base[C];
   pl->grid = std::max(1, std::min(resident, pl->nitems));
-  cudaError_t e = ensure(pl->items, sorted.size() * sizeof(WorkItem));
-  if (e == cudaSuccess) e = ensure(pl->cand_base, base.size() * sizeof(int32_t));
+  const size_t ib = sorted.size() * sizeof(WorkItem), bb = base.size() * sizeof(int32_t);
+  cudaError_t e = ensure(pl->items, ib);
+  if (e == cudaSuccess) e = ensure(pl->cand_base, bb);
+  if (e == cudaSuccess) e = cudaMallocHost(&pl->host_stage, ib + bb);
+  if (e == cudaSuccess) {
+    memcpy(pl->host_stage, sorted.data(), ib);
+    memcpy(static_cast<char*>(pl->host_stage) + ib, base.data(), bb);
+    e = cudaMemcpyAsync(pl->items.p, pl->host_stage, ib, cudaMemcpyHostToDevice, st);
+  }
   if (e == cudaSuccess)
-    e = cudaMemcpy(pl->items.p, sorted.data(), sorted.size() * sizeof(WorkItem), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess)
-    e = cudaMemcpy(pl->cand_base.p, base.data(), base.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    e = cudaMemcpyAsync(pl->cand_base.p, static_cast<char*>(pl->host_stage) + ib, bb, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) {
     *err = cuda_fail(e, "plan upload");
-    free_buf(pl->items);
-    free_buf(pl->cand_base);
-    delete pl;
+    free_plan(pl);
     return nullptr;
   }
   return pl;
 }
 
 Plan* get_plan(fpw_ctx* ctx, const int64_t* off, int64_t C, int64_t F, const TileShape& sh, int blocks_per_sm,
-               int* err) {
+               cudaStream_t st, int* err) {
   uint64_t key = fnv1a(off, sizeof(int64_t) * (size_t)(C + 1));
   key = mix(key, C);
   key = mix(key, F);
@@ -323,7 +338,7 @@ Plan* get_plan(fpw_ctx* ctx, const int64_t* off, int64_t C, int64_t F, const Til
       *err = FPW_OK;
       return p;
     }
-  Plan* p = build_plan(ctx, off, C, F, sh, blocks_per_sm, key, err);
+  Plan* p = build_plan(ctx, off, C, F, sh, blocks_per_sm, key, st, err);
   if (!p) return nullptr;
   p->use = ++ctx->tick;
   if ((int)ctx->plans.size() >= kMaxPlans) {
@@ -332,9 +347,7 @@ Plan* get_plan(fpw_ctx* ctx, const int64_t* off, int64_t C, int64_t F, const Til
     // graphs may reference the evicted plan's buffers: drop them all
     for (GraphEntry& g : ctx->graphs) cudaGraphExecDestroy(g.exec);
     ctx->graphs.clear();
-    free_buf((*it)->items);
-    free_buf((*it)->cand_base);
-    delete *it;
+    free_plan(*it);
     ctx->plans.erase(it);
   }
   ctx->plans.push_back(p);
@@ -364,6 +377,8 @@ struct BatchCall {
   int ngroups;              // several-M call: groups g (M = M_max / g); 0 = single M
   int groups[kMaxGroups];
   int32_t* topk_off;        // several-M call: offset of each reported peak
+  int32_t* bins_out;        // bin dump of frequencies [bins_k0, bins_k1), or NULL
+  int64_t bins_k0, bins_k1;
 };
 
 void drop_graphs(fpw_ctx* ctx) {
@@ -373,7 +388,6 @@ void drop_graphs(fpw_ctx* ctx) {
 
 // Enqueue prep -> persistent tile kernel -> merge -> status latch.
 int enqueue_tile_path(fpw_ctx* ctx, const BatchCall& b, Plan* pl, unsigned* words, cudaStream_t st) {
-  const bool acc64 = b.p.accum == FPW_ACCUM_FP64;
   const int64_t nobs = b.off_h[b.C];
   FPW_CK(cudaMemsetAsync(words, 0, 2 * sizeof(unsigned), st));
   FPW_CK(cudaMemsetAsync(ctx->curve_bad.p, 0, (size_t)b.C, st));
@@ -387,7 +401,7 @@ int enqueue_tile_path(fpw_ctx* ctx, const BatchCall& b, Plan* pl, unsigned* word
   pa.freqs = b.freqs;
   pa.nfreq = b.F;
   pa.aw = ctx->aw.p;
-  pa.accum64 = acc64 ? 1 : 0;
+  pa.accum = b.p.accum;
   pa.curve_bad = static_cast<uint8_t*>(ctx->curve_bad.p);
   pa.status = words + 1;
   FPW_CK(launch_prep(pa, st));
@@ -419,6 +433,10 @@ int enqueue_tile_path(fpw_ctx* ctx, const BatchCall& b, Plan* pl, unsigned* word
   ta.ngroups = b.ngroups;
   for (int q = 0; q < b.ngroups; ++q) ta.group_g[q] = b.groups[q];
   ta.group_rows = pl->nslots;
+  ta.bins_out = b.bins_out;
+  ta.bins_k0 = b.bins_k0;
+  ta.bins_k1 = b.bins_k1;
+  ta.bins_nobs = nobs;
   const bool timed = ctx->timing && !b.p.use_graph;
   if (timed) {
     while (ctx->ev.size() < ctx->ev_used + 2) {
@@ -428,7 +446,7 @@ int enqueue_tile_path(fpw_ctx* ctx, const BatchCall& b, Plan* pl, unsigned* word
     }
     FPW_CK(cudaEventRecord(ctx->ev[ctx->ev_used], st));
   }
-  FPW_CK(launch_tile(ta, pl->shape, b.p.phase_mode, acc64, pl->grid, st));
+  FPW_CK(launch_tile(ta, pl->shape, b.p.phase_mode, b.p.accum, pl->grid, st));
   if (timed) {
     FPW_CK(cudaEventRecord(ctx->ev[ctx->ev_used + 1], st));
     ctx->ev_used += 2;
@@ -457,7 +475,6 @@ int enqueue_tile_path(fpw_ctx* ctx, const BatchCall& b, Plan* pl, unsigned* word
 }
 
 int run_tile_path(fpw_ctx* ctx, const BatchCall& b) {
-  const bool acc64 = b.p.accum == FPW_ACCUM_FP64;
   int64_t max_n = 0;
   double sn = 0.0, sn2 = 0.0;
   for (int64_t c = 0; c < b.C; ++c) {
@@ -470,14 +487,17 @@ int run_tile_path(fpw_ctx* ctx, const BatchCall& b) {
   TileShape sh{};
   int rc = choose_shape(ctx, b.p, b.M, b.k, max_n, n_typ, b.ngroups, sh);
   if (rc != FPW_OK) return rc;
-  const int bps = tile_max_blocks_per_sm(sh.R, b.p.phase_mode, acc64, sh.threads, sh.smem, b.ngroups > 0);
+  const int bps = tile_max_blocks_per_sm(sh.R, b.p.phase_mode, b.p.accum, sh.threads, sh.smem, b.ngroups > 0,
+                                         b.bins_out != nullptr);
   if (bps < 1) return FPW_ENOTSUP;
-  Plan* pl = get_plan(ctx, b.off_h, b.C, b.F, sh, bps, &rc);
+  Plan* pl = get_plan(ctx, b.off_h, b.C, b.F, sh, bps, b.stream, &rc);
   if (!pl) return rc;
+  ctx->last_shape = sh;
+  ctx->last_grid = pl->grid;
   const int64_t nobs = b.off_h[b.C];
   // scratch (grow-only; growing invalidates captured graphs)
   void* before[6] = {ctx->aw.p, ctx->cand_S.p, ctx->cand_idx.p, ctx->curve_bad.p, ctx->words.p, ctx->tile_dev.p};
-  cudaError_t e = ensure(ctx->aw, (size_t)(nobs + 2) * (acc64 ? 16 : 8));
+  cudaError_t e = ensure(ctx->aw, (size_t)(nobs + 2) * accum_bin_bytes(b.p.accum));
   {
     const int64_t Wown = (int64_t)sh.threads * sh.R - 2;
     if (e == cudaSuccess) e = ensure(ctx->tile_dev, sizeof(double) * (size_t)((b.F + Wown - 1) / Wown + 1));
@@ -491,7 +511,7 @@ int run_tile_path(fpw_ctx* ctx, const BatchCall& b) {
   if (memcmp(before, after, sizeof(before)) != 0) drop_graphs(ctx);
   unsigned* words = static_cast<unsigned*>(ctx->words.p);
 
-  if (!b.p.use_graph) return enqueue_tile_path(ctx, b, pl, words, b.stream);
+  if (!b.p.use_graph || b.bins_out) return enqueue_tile_path(ctx, b, pl, words, b.stream);
 
   uint64_t gk = mix(pl->key, (const void*)b.stream);
   for (const void* q : {(const void*)b.offsets, (const void*)b.t, (const void*)b.x, (const void*)b.sigma,
@@ -587,6 +607,11 @@ int run_plain_path(fpw_ctx* ctx, const BatchCall& b) {
     a.inv_alpha2 = b.p.inv_alpha2;
     a.S_out = S;
     a.status = words + 1;
+    a.bins_out = b.bins_out;
+    a.bins_k0 = b.bins_k0;
+    a.bins_k1 = b.bins_k1;
+    a.bins_nobs = b.off_h[b.C];
+    a.bins_base = o;
     FPW_CK(launch_plain(a, b.stream));
     if (b.k > 0) {
       DenseTopkArgs d{};
@@ -643,6 +668,57 @@ fpw_ctx* default_ctx(int* rc) {
   return g_default[dev];
 }
 
+// Shared body of the batched entry points (arguments checked by the caller
+// for the parts specific to each).
+int batch_entry(fpw_ctx* ctx, void* stream, const fpw_params* params, const int64_t* offsets,
+                const int64_t* offsets_host, int64_t ncurves, const double* t, const double* x, const double* sigma,
+                const double* freqs, int64_t nfreq, int M, int k, int32_t* topk_idx, float* topk_S, double* S_out,
+                int32_t* bins_out, int64_t k0, int64_t k1) {
+  if (ncurves > 0 && !offsets) return FPW_EINVAL;
+  if (ncurves > 0 && nfreq > 0 && !freqs) return FPW_EINVAL;
+  fpw_params p;
+  fpw_params_default(&p);
+  if (params) p = *params;
+  if (!valid_params(p)) return FPW_EINVAL;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return FPW_ECUDA;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  clear_stale_error();
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  ctx->last_stream = st;
+  if (ncurves == 0) return FPW_OK;
+  const int64_t* off_h = offsets_host;
+  if (!off_h) {
+    ctx->off_host.resize((size_t)ncurves + 1);
+    FPW_CK(cudaMemcpyAsync(ctx->off_host.data(), offsets, sizeof(int64_t) * (size_t)(ncurves + 1),
+                           cudaMemcpyDeviceToHost, st));
+    FPW_CK(cudaStreamSynchronize(st));
+    off_h = ctx->off_host.data();
+  }
+  if (check_offsets(off_h, ncurves) != FPW_OK) return FPW_EINVAL;
+  if (off_h[ncurves] > 0 && (!t || !x || !sigma)) return FPW_EINVAL;
+  BatchCall b{};
+  b.stream = st;
+  b.p = p;
+  b.offsets = offsets;
+  b.off_h = off_h;
+  b.C = ncurves;
+  b.t = t;
+  b.x = x;
+  b.sigma = sigma;
+  b.freqs = freqs;
+  b.F = nfreq;
+  b.M = M;
+  b.k = k;
+  b.topk_idx = topk_idx;
+  b.topk_S = topk_S;
+  b.S_out = S_out;
+  b.bins_out = off_h[ncurves] > 0 ? bins_out : nullptr;
+  b.bins_k0 = k0;
+  b.bins_k1 = k1;
+  return batch_impl(ctx, b);
+}
+
 }  // namespace
 
 extern "C" {
@@ -658,7 +734,7 @@ void fpw_params_default(fpw_params* p) {
   p->use_graph = 0;
 }
 
-int fpw_version(void) { return 1; }
+int fpw_version(void) { return 2; }
 
 const char* fpw_strerror(int s) {
   switch (s) {
@@ -716,11 +792,7 @@ int fpw_ctx_destroy(fpw_ctx* ctx) {
     std::lock_guard<std::mutex> lk(ctx->mu);
     cudaDeviceSynchronize();
     drop_graphs(ctx);
-    for (Plan* p : ctx->plans) {
-      free_buf(p->items);
-      free_buf(p->cand_base);
-      delete p;
-    }
+    for (Plan* p : ctx->plans) free_plan(p);
     ctx->plans.clear();
     for (DevBuf* b : {&ctx->aw, &ctx->cand_S, &ctx->cand_idx, &ctx->curve_bad, &ctx->words, &ctx->dense, &ctx->tile_dev, &ctx->h_off,
                       &ctx->h_t, &ctx->h_x, &ctx->h_sigma, &ctx->h_freqs, &ctx->h_idx, &ctx->h_S, &ctx->sh_image,
@@ -749,6 +821,23 @@ int fpw_ctx_clear_shapes(fpw_ctx* ctx) {
   if (!ctx) return FPW_EINVAL;
   std::lock_guard<std::mutex> lk(ctx->mu);
   ctx->shapes.clear();
+  return FPW_OK;
+}
+
+int fpw_ctx_last_shape(fpw_ctx* ctx, int* threads, int* freqs_per_thread, int* obs_chunk, int* grid) {
+  if (!ctx || !threads || !freqs_per_thread || !obs_chunk || !grid) return FPW_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  *threads = ctx->last_shape.threads;
+  *freqs_per_thread = ctx->last_shape.R;
+  *obs_chunk = ctx->last_shape.obs_chunk;
+  *grid = ctx->last_grid;
+  return FPW_OK;
+}
+
+int fpw_ctx_set_wait_limit(fpw_ctx* ctx, int64_t clocks) {
+  if (!ctx || clocks < 0) return FPW_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  ctx->wait_clocks = (long long)clocks;
   return FPW_OK;
 }
 
@@ -792,47 +881,19 @@ int fpw_periodogram_batch_ex(fpw_ctx* ctx, void* stream, const fpw_params* param
                              const double* sigma, const double* freqs, int64_t nfreq, int M, int k,
                              int32_t* topk_idx, float* topk_S, double* S_out) {
   if (!ctx || ncurves < 0 || nfreq < 0 || M < 1 || k < 0 || k > FPW_MAX_TOPK) return FPW_EINVAL;
-  if (ncurves > 0 && !offsets) return FPW_EINVAL;
-  if (ncurves > 0 && nfreq > 0 && !freqs) return FPW_EINVAL;
   if (ncurves > 0 && k > 0 && (!topk_idx || !topk_S)) return FPW_EINVAL;
-  fpw_params p;
-  fpw_params_default(&p);
-  if (params) p = *params;
-  if (!valid_params(p)) return FPW_EINVAL;
-  DeviceGuard g(ctx->device);
-  if (!g.ok) return FPW_ECUDA;
-  std::lock_guard<std::mutex> lk(ctx->mu);
-  clear_stale_error();
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  ctx->last_stream = st;
-  if (ncurves == 0) return FPW_OK;
-  const int64_t* off_h = offsets_host;
-  if (!off_h) {
-    ctx->off_host.resize((size_t)ncurves + 1);
-    FPW_CK(cudaMemcpyAsync(ctx->off_host.data(), offsets, sizeof(int64_t) * (size_t)(ncurves + 1),
-                           cudaMemcpyDeviceToHost, st));
-    FPW_CK(cudaStreamSynchronize(st));
-    off_h = ctx->off_host.data();
-  }
-  if (check_offsets(off_h, ncurves) != FPW_OK) return FPW_EINVAL;
-  if (off_h[ncurves] > 0 && (!t || !x || !sigma)) return FPW_EINVAL;
-  BatchCall b{};
-  b.stream = st;
-  b.p = p;
-  b.offsets = offsets;
-  b.off_h = off_h;
-  b.C = ncurves;
-  b.t = t;
-  b.x = x;
-  b.sigma = sigma;
-  b.freqs = freqs;
-  b.F = nfreq;
-  b.M = M;
-  b.k = k;
-  b.topk_idx = topk_idx;
-  b.topk_S = topk_S;
-  b.S_out = S_out;
-  return batch_impl(ctx, b);
+  return batch_entry(ctx, stream, params, offsets, offsets_host, ncurves, t, x, sigma, freqs, nfreq, M, k, topk_idx,
+                     topk_S, S_out, nullptr, 0, 0);
+}
+
+int fpw_periodogram_batch_bins(fpw_ctx* ctx, void* stream, const fpw_params* params, const int64_t* offsets,
+                               const int64_t* offsets_host, int64_t ncurves, const double* t, const double* x,
+                               const double* sigma, const double* freqs, int64_t nfreq, int M, int64_t k0, int64_t k1,
+                               int32_t* bins_out, double* S_out) {
+  if (!ctx || ncurves < 0 || nfreq < 0 || M < 1 || k0 < 0 || k1 < k0 || k1 > nfreq) return FPW_EINVAL;
+  if (ncurves > 0 && k1 > k0 && !bins_out) return FPW_EINVAL;
+  return batch_entry(ctx, stream, params, offsets, offsets_host, ncurves, t, x, sigma, freqs, nfreq, M, 0, nullptr,
+                     nullptr, S_out, k1 > k0 ? bins_out : nullptr, k0, k1);
 }
 
 int fpw_periodogram_batch_multi(fpw_ctx* ctx, void* stream, const fpw_params* params, const int64_t* offsets,
@@ -1106,6 +1167,7 @@ int fpw_periodogram_shared(fpw_ctx* ctx, void* stream, const fpw_params* params,
   a.curve_bad = static_cast<uint8_t*>(ctx->curve_bad.p);
   a.S32 = k > 0 ? static_cast<float*>(ctx->sh_S32.p) : nullptr;
   a.status = words + 1;
+  a.wait_clocks = ctx->wait_clocks;
   if (ctx->timing) {
     while (ctx->ev.size() < ctx->ev_used + 2) {
       cudaEvent_t e;
@@ -1155,10 +1217,13 @@ int fpw_periodogram_drift(fpw_ctx* ctx, void* stream, const fpw_params* params, 
   if (R == 0) R = (K <= 1 && drift_fits(M, K, T, 2, ctx->smem_optin)) ? 2 : 1;
   if (!drift_fits(M, K, T, R, ctx->smem_optin)) return FPW_ENOTSUP;
   if (ncurves == 0) return FPW_OK;
-  int64_t nobs = 0;
-  FPW_CK(cudaMemcpyAsync(&nobs, offsets + ncurves, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  // every offset is checked before a kernel indexes the observations with it
+  ctx->off_host.resize((size_t)ncurves + 1);
+  FPW_CK(cudaMemcpyAsync(ctx->off_host.data(), offsets, sizeof(int64_t) * (size_t)(ncurves + 1),
+                         cudaMemcpyDeviceToHost, st));
   FPW_CK(cudaStreamSynchronize(st));
-  if (nobs < 0) return FPW_EINVAL;
+  if (check_offsets(ctx->off_host.data(), ncurves) != FPW_OK) return FPW_EINVAL;
+  const int64_t nobs = ctx->off_host[(size_t)ncurves];
   if (nobs > 0 && (!t || !x || !sigma)) return FPW_EINVAL;
   unsigned* words = static_cast<unsigned*>(ctx->words.p);
   if (nfreq == 0) {
@@ -1238,33 +1303,6 @@ int fpw_phase_entropy_peaks(fpw_ctx* ctx, void* stream, const int64_t* offsets, 
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   ctx->last_stream = st;
   FPW_CK(launch_entropy_peaks(offsets, ncurves, t, freqs, nfreq, M, k, topk_idx, H_out, z_out, st));
-  return FPW_OK;
-}
-
-int fpw_debug_bins(fpw_ctx* ctx, void* stream, const fpw_params* params, const double* t, int64_t n,
-                   const double* freqs, int64_t nfreq, int M, int32_t* bins_out) {
-  if (!ctx || n < 0 || nfreq < 0 || M < 1) return FPW_EINVAL;
-  if (n > 0 && nfreq > 0 && (!t || !freqs || !bins_out)) return FPW_EINVAL;
-  fpw_params p;
-  fpw_params_default(&p);
-  if (params) p = *params;
-  if (!valid_params(p)) return FPW_EINVAL;
-  DeviceGuard g(ctx->device);
-  if (!g.ok) return FPW_ECUDA;
-  std::lock_guard<std::mutex> lk(ctx->mu);
-  clear_stale_error();
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  ctx->last_stream = st;
-  DebugBinsArgs a{};
-  a.t = t;
-  a.n = n;
-  a.freqs = freqs;
-  a.nfreq = nfreq;
-  a.M = M;
-  a.phase_mode = p.phase_mode;
-  a.anchor_every = p.phase_mode == FPW_PHASE_FP32 ? p.K : 512;
-  a.bins = bins_out;
-  FPW_CK(launch_debug_bins(a, st));
   return FPW_OK;
 }
 

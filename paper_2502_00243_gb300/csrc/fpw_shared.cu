@@ -52,7 +52,7 @@ constexpr int kShHOperandMax = kShNMax * kShK * 2;   // one H operand of a chunk
 constexpr int kShHSlotBytes = 2 * kShHOperandMax;    // two H operands (two accumulators)
 constexpr int kShTmemCols = 512;
 constexpr unsigned kOneOne = 0x3C003C00u;       // two fp16 1.0
-constexpr long long kWaitClocks = 4000000000LL; // ~2 s at 2 GHz
+constexpr long long kWaitClocks = 4000000000LL; // default wait limit, ~2 s at 2 GHz
 // A waiting thread is suspended in mbarrier.try_wait until the phase completes
 // or this many nanoseconds pass (so waiting warps do not take issue slots).
 constexpr uint32_t kSuspendNs = 20000u;
@@ -122,18 +122,21 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   }
 }
 
-// mbarrier wait that also gives up when another role of the CTA set *abort.
-__device__ __forceinline__ bool mbar_wait_ab(uint64_t* bar, uint32_t parity, volatile int* abort) {
+// mbarrier wait of the chunk pipeline: gives up after `limit` clocks or when
+// another role of the CTA set *abort; `suspend_ns` is the longest time one
+// try_wait may suspend the thread.
+__device__ __forceinline__ bool mbar_wait_ab(uint64_t* bar, uint32_t parity, volatile int* abort, long long limit,
+                                             uint32_t suspend_ns) {
   const long long t0 = clock64();
   while (true) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
         : "=r"(done)
-        : "r"(smem_addr(bar)), "r"(parity), "r"(kSuspendNs)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(suspend_ns)
         : "memory");
     if (done) return true;
-    if (*abort || clock64() - t0 > kWaitClocks) return false;
+    if (*abort || clock64() - t0 > limit) return false;
   }
 }
 
@@ -387,6 +390,11 @@ __global__ void __launch_bounds__(kShThreads, 1) shared_mma_kernel(const SharedA
   fence_after_sync();
   const uint32_t tmem = *tslot;
   bool fail = false;
+  // limit of the pipeline's waits (the drain after a failure keeps the
+  // default); a limit far below one suspension also stops each try_wait from
+  // suspending, so that a wait whose phase is not complete gives up at once
+  const long long wait_limit = a.wait_clocks > 0 ? a.wait_clocks : kWaitClocks;
+  const uint32_t suspend_ns = wait_limit < 100000 ? 0u : kSuspendNs;
 
   if (warp >= kShBuilderWarps) {
     // ------------------------------------------------------------ issuers: warp 16 drives accumulator 0 and
@@ -421,18 +429,18 @@ __global__ void __launch_bounds__(kShThreads, 1) shared_mma_kernel(const SharedA
       int64_t ch = 0;
       for (int64_t gc = 0; gc < total && !fail; ++gc, ch = (ch + 1 == nch) ? 0 : ch + 1) {
         const int s = (int)(gc & 1), vs = (int)(gc & (kShVSlots - 1));
-        if (!mbar_wait_ab(&bar_full[s], (ph_full >> s) & 1u, s_abort)) { fail = true; break; }
+        if (!mbar_wait_ab(&bar_full[s], (ph_full >> s) & 1u, s_abort, wait_limit, suspend_ns)) { fail = true; break; }
         ph_full ^= 1u << s;
         if (iop == 0 && gc + 2 < total) {  // its slot was last read by the MMAs of gc - 2, done before `full` of gc
           const int v2 = (int)((gc + 2) & (kShVSlots - 1));
           load_next(v2);
           v_out |= 1u << v2;
         }
-        if (!mbar_wait_ab(&bar_v[vs], (ph_v >> vs) & 1u, s_abort)) { fail = true; break; }
+        if (!mbar_wait_ab(&bar_v[vs], (ph_v >> vs) & 1u, s_abort, wait_limit, suspend_ns)) { fail = true; break; }
         ph_v ^= 1u << vs;
         v_out &= ~(1u << vs);
         if (ch == 0 && gc > 0) {  // the previous item's accumulators have been read
-          if (!mbar_wait_ab(bar_tfree, ph_tfree, s_abort)) { fail = true; break; }
+          if (!mbar_wait_ab(bar_tfree, ph_tfree, s_abort, wait_limit, suspend_ns)) { fail = true; break; }
           ph_tfree ^= 1u;
         }
         fence_after_sync();
@@ -499,7 +507,7 @@ __global__ void __launch_bounds__(kShThreads, 1) shared_mma_kernel(const SharedA
           builders_sync(kShBuilders);
         }
         if (!fail && gc >= 2) {  // the MMAs of gc - 2 read H slot s
-          fail = !mbar_wait_ab(&bar_empty[s], (ph_empty >> s) & 1u, s_abort);
+          fail = !mbar_wait_ab(&bar_empty[s], (ph_empty >> s) & 1u, s_abort, wait_limit, suspend_ns);
           ph_empty ^= 1u << s;
         }
         fail = __any_sync(0xffffffffu, fail);
@@ -556,7 +564,7 @@ __global__ void __launch_bounds__(kShThreads, 1) shared_mma_kernel(const SharedA
       // through shared memory.
       float* sPart = reinterpret_cast<float*>(smem + kOffPart);
       if (!fail && nch > 0) {
-        fail = !mbar_wait_ab(bar_acc, ph_acc, s_abort);
+        fail = !mbar_wait_ab(bar_acc, ph_acc, s_abort, wait_limit, suspend_ns);
         fence_after_sync();
       }
       fail = __any_sync(0xffffffffu, fail);

@@ -37,6 +37,7 @@ struct SharedArgs {
   float* topk_S;
   cudaEvent_t timing_start; // optional events around the MMA kernel
   cudaEvent_t timing_stop;
+  long long wait_clocks;    // limit of each pipeline wait in SM clocks (0: the default, about 2 s)
 };
 
 // Per-curve top-k peaks of a dense FP32 periodogram [ncurves][nfreq] (one block per curve).

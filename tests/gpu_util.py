@@ -38,6 +38,48 @@ def run_batch(ctx, w, *, M=None, k=None, params=None, dense=False, d=None):
             Sd.cpu().numpy().reshape(C, F) if dense else None, st)
 
 
+def run_bins(ctx, w, k0, k1, *, M=None, params=None, d=None, dense=False):
+    """Bins that the periodogram kernel itself gave every observation of the
+    batch at frequencies k0 <= k < k1 (fpw_periodogram_batch_bins; the same
+    launch as the batched call): int32 ``[k1 - k0, nobs]``, -1 where nothing was
+    written; with ``dense`` also S ``[C, F]``."""
+    d = d or to_dev(w)
+    M = w.M if M is None else M
+    nobs = int(w.offsets[-1])
+    out = torch.full(((k1 - k0) * nobs,), -1, dtype=torch.int32, device="cuda")
+    Sd = torch.empty(w.ncurves * w.nfreq, dtype=torch.float64, device="cuda") if dense else None
+    G.fpw_periodogram_batch_bins(ctx, None, params, d["offsets"], w.offsets, d["t"], d["x"], d["sigma"], d["freqs"],
+                                 M, k0, k1, out, Sd)
+    torch.cuda.synchronize()
+    st = ctx.status()
+    return (out.cpu().numpy().reshape(k1 - k0, nobs), Sd.cpu().numpy().reshape(w.ncurves, w.nfreq) if dense else None,
+            st)
+
+
+def bin_mismatches(g_bins, w, k0, k1, M, oracle_bins, curves=None):
+    """Compare kernel bins ``[k1 - k0, nobs]`` of the batch ``w`` with the oracle's,
+    curve by curve: (pairs, mismatches, mismatches farther than 1e-9 cycles
+    from a bin edge, largest edge distance of a mismatch). Every pair must have
+    been written."""
+    pairs = mism = far = 0
+    worst = 0.0
+    fr = w.freqs[k0:k1]
+    for c in (range(w.ncurves) if curves is None else curves):
+        o0, o1 = int(w.offsets[c]), int(w.offsets[c + 1])
+        if o1 == o0:
+            continue
+        g = g_bins[:, o0:o1]
+        assert (g >= 0).all() and (g < M).all(), f"curve {c}: unwritten or out-of-range bins"
+        b, e = oracle_bins(w.t[o0:o1], fr, M)
+        mm = g != b
+        pairs += mm.size
+        mism += int(mm.sum())
+        far += int((mm & (e > 1e-9)).sum())
+        if mm.any():
+            worst = max(worst, float(e[mm].max()))
+    return pairs, mism, far, worst
+
+
 def run_single(ctx, t, x, sigma, freqs, M, params=None):
     tt = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda() for a in (t, x, sigma, freqs)]
     S = torch.empty(tt[3].numel(), dtype=torch.float64, device="cuda")

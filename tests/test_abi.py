@@ -58,6 +58,10 @@ def test_null_context_rejected_without_touching_a_gpu(lib):
     assert lib.fpw_periodogram_batch_ex(None, None, None, None, None, 0, None, None, None, None, 0, 1, 0, None, None,
                                         None) == G.FPW_EINVAL
     assert lib.fpw_ctx_status(None) == G.FPW_EINVAL
+    assert lib.fpw_periodogram_batch_bins(None, None, None, None, None, 0, None, None, None, None, 0, 1, 0, 0, None,
+                                          None) == G.FPW_EINVAL
+    v = [ctypes.c_int() for _ in range(4)]
+    assert lib.fpw_ctx_last_shape(None, *[ctypes.byref(q) for q in v]) == G.FPW_EINVAL
     assert lib.fpw_ctx_destroy(None) == G.FPW_OK
     assert lib.fpw_ctx_create(None, 0) == G.FPW_EINVAL
     h = vp()

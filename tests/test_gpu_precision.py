@@ -1,23 +1,40 @@
-"""Precision study on the 2000-day, 500 1/d workload (t f up to 10^6 cycles) and
-autotuner parity, on the GPU against the oracle.
+"""Precision study on the GPU against the oracle, at the stated size of the
+2000-day workload: 100 curves of 1500 observations, 2e6 linear frequencies
+0.01-500 1/d (t f up to 1e6 cycles), M = 20, per phase mode -- binary64 direct
+(the plain form), the exact 64-bit fixed-point default, and the FP32 phase
+re-anchored every K in {64, 256, 1024} frequencies.
 
-Per phase mode: the bin-mismatch rate (kernel bins vs oracle bins), how many
-mismatches sit farther than 1e-9 cycles from an edge, and the S relative error
-on windows of the 2e6-point grid near 100, 250, 400 and 499 1/d."""
+* S: each curve's dense periodogram from one launch over the full grid,
+  against the oracle at every 8th grid frequency (the oracle evaluates each
+  frequency directly, so the sampled frequencies carry exactly the values of
+  the full grid; 100 x 1500 x 2.5e5 = 3.75e10 oracle evaluations): largest and
+  median relative error, away from bin edges (1e-9 cycles).
+* Bins: the bins the periodogram kernel itself gave (fpw_periodogram_batch_bins,
+  the launch that also writes S) for all 100 curves in windows of 512
+  frequencies near 100, 250, 400 and 499 1/d (3.1e8 pairs; the plain form's
+  launch takes seconds, so it is checked on the window near 499 1/d), against
+  the oracle's bins and exact edge distances: mismatch count and rate, and how
+  many lie farther than 1e-9 cycles from an edge.
+
+FPW_PRECISION_REPORT=<file> appends one JSON line per mode."""
 from __future__ import annotations
+
+import json
+import os
 
 import numpy as np
 import pytest
 
 import lightcurves as L
 import oracle
-from gpu_util import assert_S_close, check_topk, run_batch, run_single, s_bound
+from gpu_util import assert_S_close, bin_mismatches, check_topk, run_batch, run_bins, s_bound, to_dev
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 WINDOWS = (100.0, 250.0, 400.0, 499.0)
-NWIN = 2048
+NWIN = 512
+STRIDE = 8
 
 
 @pytest.fixture(scope="module")
@@ -28,45 +45,64 @@ def G():
     return G_
 
 
-def _study(G, ctx, mode, K):
-    w = L.make("precision", range(3))
-    full = L.freq_grid("precision")
+@pytest.fixture(scope="module")
+def work():
+    w = L.make("precision")
+    cores = os.cpu_count() or 1
+    fs = w.freqs[::STRIDE]
+    S_or, _, _ = oracle.fpw_batch(w.offsets, w.t, w.x, w.sigma, fs, w.M, nthreads=cores)
+    near = np.stack([oracle.min_edge_parallel(w.curve(c)[0], fs, w.M, nthreads=cores) <= 1e-9
+                     for c in range(w.ncurves)])
+    return w, S_or, near
+
+
+MODES = [("fixed64", 0, 256), ("fp64-plain", 1, 256), ("fp32 K=64", 2, 64), ("fp32 K=256", 2, 256),
+         ("fp32 K=1024", 2, 1024)]
+
+
+@pytest.mark.parametrize("name,mode,K", MODES, ids=[m[0] for m in MODES])
+def test_precision_study_full_size(G, work, name, mode, K):
+    w, S_or, near = work
+    ctx = G.Context(0)
+    d = to_dev(w)
     p = G.fpw_params_default(phase_mode=mode, K=K)
-    total = far = bad_S = 0
+    windows = WINDOWS[-1:] if mode == G.FPW_PHASE_FP64 else WINDOWS
+    pairs = mism = far = 0
+    worst = 0.0
+    Sd = None
+    for f0 in windows:
+        k0 = int(np.searchsorted(w.freqs, f0))
+        g, S_full, st = run_bins(ctx, w, k0, k0 + NWIN, params=p, d=d, dense=Sd is None)
+        assert st == 0
+        if Sd is None:
+            Sd = S_full[:, ::STRIDE]
+        a, b, c, e = bin_mismatches(g, w, k0, k0 + NWIN, w.M, oracle.bins)
+        pairs, mism, far, worst = pairs + a, mism + b, far + c, max(worst, e)
     errs = []
     for c in range(w.ncurves):
         t, x, s = w.curve(c)
-        for f0 in WINDOWS:
-            a = int(np.searchsorted(full, f0))
-            fr = full[a:a + NWIN]
-            tt, ff = torch.from_numpy(t).cuda(), torch.from_numpy(fr).cuda()
-            out = torch.empty(NWIN * t.size, dtype=torch.int32, device="cuda")
-            G.fpw_debug_bins(ctx, None, p, tt, ff, w.M, out)
-            g = out.cpu().numpy().reshape(NWIN, t.size)
-            b, e = oracle.bins(t, fr, w.M)
-            mm = g != b
-            total += int(mm.sum())
-            far += int((mm & (e > 1e-9)).sum())
-            S_or = oracle.fpw(t, x, s, fr, w.M)
-            S_g, st = run_single(ctx, t, x, s, fr, w.M, p)
-            assert st == 0
-            errs.append(np.abs(S_g - S_or) / np.maximum(np.abs(S_or), 1e-300))
+        ok = ~near[c] & (np.abs(S_or[c]) > 1e-6 * s_bound(x, s))
+        errs.append(np.abs(Sd[c][ok] - S_or[c][ok]) / np.abs(S_or[c][ok]))
+        if mode == G.FPW_PHASE_FIXED64:
+            assert_S_close(Sd[c], S_or[c], s_bound(x, s), mask=~near[c], what=f"{name} curve {c}")
+        if mode == G.FPW_PHASE_FP64:  # the same binary64 operations as the oracle
+            np.testing.assert_array_equal(Sd[c], S_or[c])
     errs = np.concatenate(errs)
-    pairs = w.ncurves * len(WINDOWS) * NWIN * 1500
-    return total, far, pairs, float(errs.max()), float(np.median(errs))
-
-
-@pytest.mark.parametrize("mode,K", [(0, 256), (1, 256), (2, 64), (2, 256), (2, 1024)])
-def test_precision_study(G, mode, K):
-    ctx = G.Context(0)
-    total, far, pairs, emax, emed = _study(G, ctx, mode, K)
-    name = {0: "fixed64", 1: "fp64-plain", 2: f"fp32 K={K}"}[mode]
-    print(f"\n[precision] {name:14s} mismatches {total} / {pairs} ({total / pairs:.2e}); beyond 1e-9 cycles: {far}; "
-          f"S rel err max {emax:.2e} median {emed:.2e}")
-    if mode == 0:
-        assert far == 0 and emed < 1e-5
-    if mode == 1:
-        assert total == 0 and emax == 0.0
+    rep = dict(mode=name, curves=w.ncurves, nobs=int(w.nobs), nfreq=int(w.nfreq), M=w.M, K=K,
+               bin_pairs=pairs, bin_mismatch=mism, bin_mismatch_rate=mism / pairs, mismatch_beyond_1e9=far,
+               worst_mismatch_edge_distance=worst, S_compared=int(errs.size), S_rel_err_max=float(errs.max()),
+               S_rel_err_median=float(np.median(errs)))
+    print(f"\n[precision] {json.dumps(rep)}")
+    path = os.environ.get("FPW_PRECISION_REPORT")
+    if path:
+        with open(path, "a") as fh:
+            fh.write(json.dumps(rep) + "\n")
+    if mode == G.FPW_PHASE_FIXED64:
+        assert far == 0
+    elif mode == G.FPW_PHASE_FP64:
+        assert mism == 0
+    else:  # FP32 phase: mismatches only within its analytic margin of an edge
+        assert worst <= (2 * K + 4) * 2.0 ** -24
     ctx.close()
 
 

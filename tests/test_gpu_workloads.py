@@ -3,10 +3,13 @@ the oracle on sampled curves.
 
 Per workload: the whole batch runs once with the default parameters and top-k;
 for stratified sample curves the oracle computes the dense periodogram over the
-full grid, which checks the top-k of the full launch (tie-aware) and the dense S
-of a launch over the sample (away from bin edges); the bins of the sample's
-observations at the grid's highest frequencies (largest t f) are compared one
-by one. With FPW_WORKLOAD_REPORT set to a path, one JSON line per workload is
+full grid, which checks the top-k of the full launch (tie-aware; identical
+indices wherever the oracle's neighbouring ranked peaks differ by more than the
+S tolerance) and the dense S of a launch over the sample (away from bin edges);
+the bins that the periodogram kernel gave the sample's observations at the
+grid's highest frequencies (largest t f) -- dumped by a launch over the sample
+with the kernel shape of the full launch, so with the same tiles, anchors and
+stepping -- are compared one by one. With FPW_WORKLOAD_REPORT set to a path, one JSON line per workload is
 appended there: pairs compared, bin mismatches (and how many lie farther than
 1e-9 cycles from an edge), S relative error, exact top-k agreement and the
 oracle's own evaluation rate on the host cores."""
@@ -21,7 +24,7 @@ import pytest
 
 import lightcurves as L
 import oracle
-from gpu_util import assert_S_close, check_topk, run_batch, s_bound, to_dev
+from gpu_util import assert_S_close, bin_mismatches, check_topk, run_batch, run_bins, s_bound, to_dev
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -62,16 +65,21 @@ def test_workload_full_size_sampled(G, name, make):
     ctx = G.Context(0)
     idx, Sk, _, st = run_batch(ctx, w)  # the full batch, as the benchmark launches it
     assert st == 0
+    T, R, NC, _ = ctx.last_shape()
+    same_tiles = G.fpw_params_default(threads=T, freqs_per_thread=R, obs_chunk=NC)
     pick = stratified(w.offsets, SAMPLE)
     sub = w.subset(pick)
     _, _, Sd, st = run_batch(ctx, sub, dense=True)
     assert st == 0
+    k0 = w.nfreq - NWIN
+    g_bins, _, st = run_bins(ctx, sub, k0, w.nfreq, params=same_tiles)
+    assert st == 0
     cores = os.cpu_count() or 1
     rep = dict(workload=name, curves=int(w.ncurves), nobs=int(w.offsets[-1]), nfreq=int(w.nfreq), M=M, k=k,
                sample_curves=[int(c) for c in pick], pairs=0, bin_mismatch=0, mismatch_beyond_1e9=0,
-               topk_exact=0, topk_curves=0, oracle_evals=0.0, oracle_seconds=0.0, cores=cores)
+               topk_exact=0, topk_separated=0, topk_curves=0, oracle_evals=0.0, oracle_seconds=0.0, cores=cores,
+               shape=dict(threads=T, freqs_per_thread=R, obs_chunk=NC))
     errs = []
-    fr_top = w.freqs[-NWIN:]
     for j, c in enumerate(pick):
         t, x, s = sub.curve(j)
         t0 = time.perf_counter()
@@ -87,17 +95,23 @@ def test_workload_full_size_sampled(G, name, make):
         o_idx, o_S = oracle.topk(S_or, k + 4)
         check_topk(idx[c], Sk[c], o_idx, o_S, abs_tol=1e-7 * bound, o_dense=S_or, what=f"{name} curve {c} peaks")
         rep["topk_curves"] += 1
-        rep["topk_exact"] += int(np.array_equal(idx[c], o_idx[:k]))
-        if t.size:
-            tt, ff = torch.from_numpy(t).cuda(), torch.from_numpy(fr_top).cuda()
-            out = torch.empty(fr_top.size * t.size, dtype=torch.int32, device="cuda")
-            G.fpw_debug_bins(ctx, None, None, tt, ff, M, out)
-            gb = out.cpu().numpy().reshape(fr_top.size, t.size)
-            ob, e = oracle.bins(t, fr_top, M)
-            mm = gb != ob
-            rep["pairs"] += int(mm.size)
-            rep["bin_mismatch"] += int(mm.sum())
-            rep["mismatch_beyond_1e9"] += int((mm & (e > 1e-9)).sum())
+        exact = bool(np.array_equal(idx[c], o_idx[:k]))
+        rep["topk_exact"] += int(exact)
+        # where every ranked peak (and the first one below the list) is
+        # separated from the next by more than the S tolerance, the indices
+        # are unique and must be identical
+        ov = o_S[:k + 1]
+        tol = 1e-4 * np.abs(ov) + 1e-7 * bound
+        oi = o_idx[:k + 1]
+        sharp = all(abs(S_or[i] - S_or[q]) > 2 * (1e-4 * abs(S_or[i]) + 1e-7 * bound)
+                    for i in oi[:k] for q in (i - 1, i + 1) if 0 <= q < w.nfreq)
+        if np.all(oi >= 0) and sharp and np.all(np.abs(np.diff(ov)) > 2 * (tol[:-1] + tol[1:])):
+            rep["topk_separated"] += 1
+            assert exact, f"{name} curve {c}: separated peaks {o_idx[:k]} vs gpu {idx[c]}"
+        a, b, e_, _ = bin_mismatches(g_bins, sub, k0, w.nfreq, M, oracle.bins, curves=[j])
+        rep["pairs"] += a
+        rep["bin_mismatch"] += b
+        rep["mismatch_beyond_1e9"] += e_
     assert rep["mismatch_beyond_1e9"] == 0
     e = np.concatenate(errs) if errs else np.zeros(1)
     rep.update(S_rel_err_max=float(e.max()), S_rel_err_median=float(np.median(e)),
