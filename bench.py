@@ -49,7 +49,7 @@ SWEEP_MS = (10, 20, 50)  # bin counts of the throughput sweep
 # from DRAM once per launch (t and the staged weights, about 16.7 B per observation; per-tile re-reads
 # hit L2), so a full launch adds only the larger grid (8 B per extra frequency). Valid only for the
 # kernel source it was measured on (sha256 prefix of the tile-kernel sources, tile_source_hash).
-TILE_TRAFFIC = {"source_sha256_16": None, "bytes": None, "nfreq": 20_000}
+TILE_TRAFFIC = {"source_sha256_16": "0765efc38faeab50", "bytes": 143.09e6, "nfreq": 20_000}
 
 
 # ---------------------------------------------------------------- workload generation (spawned workers)
@@ -609,6 +609,8 @@ def run_configs(args):
             line["graph_evals_per_s_call"] = gr
         print(json.dumps(line), flush=True)
 
+    if want("accum"):
+        run_configs_accum(ctx, peak)
     if want("shared"):
         run_configs_shared(ctx, peak)
     if want("drift"):
@@ -619,6 +621,24 @@ def run_configs(args):
         run_configs_entropy(ctx, peak)
     ctx.close()
     return 0
+
+
+def run_configs_accum(ctx, peak):
+    """The bin-sum modes on one 1e4-curve batch of the sweep at M = 20: FP32
+    sums, compensated FP32 sums (16-byte bins, two-sum per addition) and
+    binary64 sums; tile-kernel rate and roofline fraction of each (the roof is
+    the 8-byte bin pair's; 16-byte bins halve it)."""
+    import lightcurves as L
+    import paper_2502_00243_gb300 as G
+    w = L.make("sweep_100k", range(10_000), M=20)
+    for name, acc in (("f32", G.FPW_ACCUM_FP32), ("f32 compensated", G.FPW_ACCUM_FP32_COMP),
+                      ("binary64", G.FPW_ACCUM_FP64)):
+        call_rate, kern_rate, ms = timed_batch(ctx, w, 20, w.k, G.fpw_params_default(accum=acc))
+        T, R, NC, grid = ctx.last_shape()
+        print(json.dumps({"config": f"sweep_100k/M=20 (batch of 1e4 curves), {name} bin sums", "accum": name,
+                          "shape": dict(threads=T, freqs_per_thread=R, obs_chunk=NC), "ms_per_call": ms,
+                          "evals_per_s_call": call_rate, "evals_per_s_tile_kernel": kern_rate,
+                          "roofline_frac": (kern_rate / peak) if kern_rate else None}), flush=True)
 
 
 def run_configs_shared(ctx, peak):
@@ -885,7 +905,7 @@ def main(argv=None):
     ap.add_argument("--no-per-m", action="store_true", help="skip the M = 10 / 50 lines of the sweep")
     ap.add_argument("--autotune", action="store_true", help="measure and install tuned kernel shapes before timing")
     ap.add_argument("--configs", nargs="?", const="all", default=None,
-                    choices=["all", "batch", "shared", "drift", "multi", "entropy"],
+                    choices=["all", "batch", "accum", "shared", "drift", "multi", "entropy"],
                     help="report every workload (one JSON line each) instead, or one section of them")
     ap.add_argument("--case", choices=["shared", "drift", "multi", "entropy"],
                     help="one small call of that path (profiling case)")

@@ -20,17 +20,11 @@
 //      significands, and the step D_i = frac(t_i * df) (df = grid spacing).
 //      Both are staged in shared memory with the prep kernel's weights
 //      (a_i = x_i w_i, w_i).
-//   2. Hot loop: Phi = Phi_s + j D_i (mod 2^64) for tile position j, bin
-//      m = floor(M * Phi_hi / 2^32), A_m += a_i, B_m += w_i in a thread-private
-//      [r][m][thread] bin array in shared memory (bank = owning thread's lane:
-//      conflict-free). The observations are taken 32 at a time: lane l holds
-//      observation l of the group in registers and, in step s = 0..31, adds it
-//      into the bins of the warp's column (l - s) mod 32 (that column's R
-//      frequencies). Every step the 32 lanes touch 32 distinct columns (one
-//      bank each, no conflicts), and after 32 steps every column has received
-//      all 32 observations, so no per-observation broadcast read is needed;
-//      a __syncwarp separates the steps. The last cnt mod 32 observations of a
-//      chunk are read by every thread (broadcast) and added into its own column.
+//   2. Hot loop (per observation, per thread, per r): Phi = Phi_s + (j*R + r) D_i
+//      (mod 2^64), bin m = floor(M * Phi_hi / 2^32), A_m += a_i, B_m += w_i in a
+//      thread-private [r][m][thread] bin array in shared memory (bank = lane,
+//      so conflict-free), all R loads issued before the R stores; every thread
+//      reads each staged observation (a warp-uniform broadcast).
 //   3. Reduce: S = sum_m A_m^2 / (B_m + 1/alpha^2), empty bins contribute 0.
 //      Several-M kernel: in-place prefix sums of the M_max bins, then for each
 //      group g the windows of g consecutive bins (circularly) for every offset;
@@ -240,7 +234,6 @@ struct Block {
   using Bin = typename P::Bin;
   using In = typename P::In;
   unsigned char* my_bins;    // this thread's column of the [r][m][thread] bin array
-  unsigned char* warp_bins;  // column 0 of this warp
   ulonglong2* sPD;           // staged {Phi_s, D} per observation
   In* sAW;                   // staged weights per observation
   double* candS;
@@ -271,7 +264,6 @@ __device__ __forceinline__ Block<P> make_block(unsigned char* smem, const TileAr
   b.W = b.T * R;
   const TileLayout L = tile_layout(b.T, R, b.M, b.NC, sizeof(Bin), args.ngroups);
   b.my_bins = smem + L.bins + (size_t)b.tid * sizeof(Bin);
-  b.warp_bins = smem + L.bins + (size_t)b.warp * 32 * sizeof(Bin);
   b.sPD = reinterpret_cast<ulonglong2*>(smem + L.pd);
   b.sAW = reinterpret_cast<typename P::In*>(smem + L.aw);
   b.candS = reinterpret_cast<double*>(smem + L.candS);
@@ -362,60 +354,71 @@ __device__ __forceinline__ void accumulate_tile(const TileArgs& args, const Bloc
     staged_lin = lin;
     __syncthreads();
     if (lin && PHASE == FPW_PHASE_FIXED64) {
-      // Rotated groups of 32 observations (see the file header): lane l adds
-      // observation g + l into the bins of column (l - step) mod 32 of its warp.
-      const int lane = b.lane;
-      const unsigned jw = (unsigned)b.warp * 32u * (unsigned)R;  // tile position of the warp's column 0
-      unsigned char* const wb = b.warp_bins;
-      const int nfull = cnt & ~31;
-      if (nfull > 0) {
-        ulonglong2 pdn = sPD[lane];
-        In xn = sAW[lane];
-        for (int g = 0; g < nfull; g += 32) {
-          const ulonglong2 pd = pdn;
-          const In xv = xn;
-          if (g + 32 < nfull) {  // next group's records, loaded while this group runs
-            pdn = sPD[g + 32 + lane];
-            xn = sAW[g + 32 + lane];
-          }
-          const unsigned long long D = pd.y;
-          const unsigned long long DR = (unsigned long long)R * D;
-          const unsigned long long P0 = pd.x + (unsigned long long)jw * D;
-#pragma unroll 2
-          for (int st = 0; st < 32; ++st) {
-            const unsigned col = (unsigned)(lane - st) & 31u;
-            const unsigned long long phi = P0 + (unsigned long long)col * DR;
-            unsigned char* const cb = wb + col * (unsigned)sizeof(Bin);
-            unsigned m[R];
-#pragma unroll
-            for (int r = 0; r < R; ++r) m[r] = bin_of_phase(phi + (unsigned long long)r * D, M);
-            Bin v[R];
-#pragma unroll
-            for (int r = 0; r < R; ++r) v[r] = *reinterpret_cast<const Bin*>(cb + m[r] * T8 + (unsigned)r * MT8);
-#pragma unroll
-            for (int r = 0; r < R; ++r)
-              *reinterpret_cast<Bin*>(cb + m[r] * T8 + (unsigned)r * MT8) = bin_add(v[r], xv);
-            if (DUMP) dump_bins<R>(args, b.W, s, wi, base + o + g + lane, jw + col * (unsigned)R, m);
-            __syncwarp();
-          }
-        }
-      }
-      // the last cnt mod 32 observations: each thread reads them all and adds
-      // them into its own column
-      for (int i = nfull; i < cnt; ++i) {
-        const ulonglong2 pd = sPD[i];
-        const In xv = sAW[i];
-        const unsigned long long phi0 = pd.x + (unsigned long long)j0 * pd.y;
+      // Every thread reads each staged observation (a warp-uniform broadcast)
+      // and adds it into its own column. The next observation's staged data
+      // is loaded before this one's bin stores (the compiler cannot move it
+      // there itself: both are shared memory), so the broadcast-load latency
+      // overlaps the bin updates.
+      if (R == 2) {
+        // Software-pipelined (measured faster only at R = 2, where the phase ->
+        // bin -> offset chain is a larger share of each iteration): the bins
+        // of observation i + 1 are computed while observation i's bin loads
+        // are in flight, from staged data loaded one iteration earlier. Same
+        // adds in the same order as the loop below.
         unsigned m[R];
+        {
+          const ulonglong2 p0 = sPD[0];
+          const unsigned long long f0 = p0.x + (unsigned long long)j0 * p0.y;
 #pragma unroll
-        for (int r = 0; r < R; ++r) m[r] = bin_of_phase(phi0 + (unsigned long long)r * pd.y, M);
-        Bin v[R];
+          for (int r = 0; r < R; ++r) m[r] = bin_of_phase(f0 + (unsigned long long)r * p0.y, M);
+        }
+        In xv = sAW[0];
+        ulonglong2 pdn = sPD[cnt > 1 ? 1 : 0];
+        In xn = sAW[cnt > 1 ? 1 : 0];
+        for (int i = 0; i < cnt; ++i) {
+          const int i2 = (i + 2 < cnt) ? i + 2 : cnt - 1;
+          const ulonglong2 pdnn = sPD[i2];
+          const In xnn = sAW[i2];
+          Bin v[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = *reinterpret_cast<const Bin*>(my_bins + m[r] * T8 + (unsigned)r * MT8);
+          for (int r = 0; r < R; ++r) v[r] = *reinterpret_cast<const Bin*>(my_bins + m[r] * T8 + (unsigned)r * MT8);
+          const unsigned long long fn = pdn.x + (unsigned long long)j0 * pdn.y;
+          unsigned mn[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r)
-          *reinterpret_cast<Bin*>(my_bins + m[r] * T8 + (unsigned)r * MT8) = bin_add(v[r], xv);
-        if (DUMP) dump_bins<R>(args, b.W, s, wi, base + o + i, j0, m);
+          for (int r = 0; r < R; ++r) mn[r] = bin_of_phase(fn + (unsigned long long)r * pdn.y, M);
+#pragma unroll
+          for (int r = 0; r < R; ++r)
+            *reinterpret_cast<Bin*>(my_bins + m[r] * T8 + (unsigned)r * MT8) = bin_add(v[r], xv);
+          if (DUMP) dump_bins<R>(args, b.W, s, wi, base + o + i, j0, m);
+#pragma unroll
+          for (int r = 0; r < R; ++r) m[r] = mn[r];
+          xv = xn;
+          pdn = pdnn;
+          xn = xnn;
+        }
+      } else {
+        ulonglong2 pd = sPD[0];
+        In xv = sAW[0];
+#pragma unroll 2
+        for (int i = 0; i < cnt; ++i) {
+          const int in = (i + 1 < cnt) ? i + 1 : i;
+          const ulonglong2 pdn = sPD[in];
+          const In xn = sAW[in];
+          // the R phases are independent multiply-adds (no serial chain of 64-bit adds)
+          const unsigned long long phi0 = pd.x + (unsigned long long)j0 * pd.y;
+          unsigned m[R];
+#pragma unroll
+          for (int r = 0; r < R; ++r) m[r] = bin_of_phase(phi0 + (unsigned long long)r * pd.y, M);
+          Bin v[R];
+#pragma unroll
+          for (int r = 0; r < R; ++r) v[r] = *reinterpret_cast<const Bin*>(my_bins + m[r] * T8 + (unsigned)r * MT8);
+#pragma unroll
+          for (int r = 0; r < R; ++r)
+            *reinterpret_cast<Bin*>(my_bins + m[r] * T8 + (unsigned)r * MT8) = bin_add(v[r], xv);
+          if (DUMP) dump_bins<R>(args, b.W, s, wi, base + o + i, j0, m);
+          pd = pdn;
+          xv = xn;
+        }
       }
     } else if (lin) {  // FPW_PHASE_FP32: FP32 phase from an FP32 anchor every K frequencies
       const int K = args.K;
@@ -717,14 +720,19 @@ __global__ void __launch_bounds__(512) tile_kernel_multi(const TileArgs args) {
           int bo = 0;
           for (int o = 0; o < gs; ++o) {
             A acc = (A)0;
+            // window j spans bins [j gs + o, j gs + o + gs - 1]: its sum is
+            // Q[end] - Q[start - 1], and its end is the next window's start - 1,
+            // so one prefix value is read per window (carried in `prev`)
+            A2 prev = (o > 0) ? col[(o - 1) * st] : make_float2(0.f, 0.f);
             for (int j = 0; j < Mg; ++j) {
-              const int p0 = j * gs + o, p1 = p0 + gs - 1;
+              const int p1 = j * gs + o + gs - 1;
               A2 w;
               if (p1 < Mx) {
-                w = col[p1 * st];
-                if (p0 > 0) w = f2sub(w, col[(p0 - 1) * st]);
-              } else {  // the window wraps past bin M_max - 1 (then p0 >= 1)
-                w = bin_add(f2sub(total[r], col[(p0 - 1) * st]), col[(p1 - Mx) * st]);
+                const A2 q = col[p1 * st];
+                w = f2sub(q, prev);
+                prev = q;
+              } else {  // the last window wraps past bin M_max - 1 (then o >= 1)
+                w = bin_add(f2sub(total[r], prev), col[(p1 - Mx) * st]);
               }
               acc += bin_term(w, cal);
             }
