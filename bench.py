@@ -44,6 +44,7 @@ SM_MAX_MHZ_NOMINAL = 2070.0
 SMEM_EVALS_PER_CLK_SM = 8  # 16 B (A, B) read-modify-write per evaluation at 128 B/clk/SM
 KERNELS_PER_STEP = 5  # prep, tile_dev, tile, merge, latch
 SWEEP_MS = (10, 20, 50)  # bin counts of the throughput sweep
+ENTROPY_INST_PER_EVAL = 10.9  # thread instructions per evaluation of the dense phase-entropy kernel (ncu, M = 20)
 # DRAM bytes (read + write) of one tile-kernel launch at M = 20, from an ncu capture of a 1e4-curve sweep
 # batch over 2e4 frequencies (dram__bytes_read.sum + dram__bytes_write.sum). The kernel reads each curve
 # from DRAM once per launch (t and the staged weights, about 16.7 B per observation; per-tile re-reads
@@ -359,9 +360,11 @@ def run_gb300(args):
     Sk = torch.empty(C * k, dtype=torch.float32, device="cuda")
     ctx = G.Context(local_rank)
     tuned = None
-    if args.autotune:
+    if not args.no_autotune:  # a few seconds: shapes and schedules for the bin counts timed below
         from paper_2502_00243_gb300 import autotune
-        tuned = autotune.tune(ctx, Ms=(args.M,))
+        t_tune = time.perf_counter()
+        tuned = {"entries": autotune.tune(ctx, Ms=(args.M, *other_Ms))}
+        tuned["seconds"] = round(time.perf_counter() - t_tune, 1)
     params = G.fpw_params_default()
     stream = torch.cuda.current_stream()
     nsm = torch.cuda.get_device_properties(local_rank).multi_processor_count
@@ -779,11 +782,19 @@ def run_configs_entropy(ctx, peak):
         torch.cuda.synchronize()
         ev = float(w.t.size) * w.nfreq
         rate = ev / (e0.elapsed_time(e1) / 1e3)
+        smem_roof = 2.0 * peak  # 16 evaluations/clk/SM: a 4-byte count read-modify-write
+        issue_roof = peak / SMEM_EVALS_PER_CLK_SM * 128.0 / ENTROPY_INST_PER_EVAL
+        bind = min(smem_roof, issue_roof)
         print(json.dumps({"config": f"single_ztf times (N={w.t.size}), dense phase entropy, M={M}, "
                                     f"{w.nfreq:.0e} freqs 0.01-100 1/d", "evals": ev,
                           "ms_per_call": e0.elapsed_time(e1), "evals_per_s_call": rate,
-                          "roofline_frac": rate / (2.0 * peak), "status": ctx.status(),
-                          "note": "roof: a 4 B count read-modify-write (8 B) per evaluation, 16 evals/clk/SM"}),
+                          "roofline": {"smem_count_rmw": smem_roof, "issue": issue_roof,
+                                       "binding": "issue" if issue_roof < smem_roof else "smem",
+                                       "frac_binding": rate / bind, "frac_smem": rate / smem_roof},
+                          "status": ctx.status(),
+                          "note": f"roof terms: a 4 B count read-modify-write per evaluation (16 evals/clk/SM); "
+                                  f"128 thread instructions/clk/SM over {ENTROPY_INST_PER_EVAL} instructions per "
+                                  f"evaluation (ncu, M = 20)"}),
               flush=True)
     r = L.make("ragged_10k")
     d = [torch.from_numpy(a).cuda() for a in (r.offsets, r.t, r.x, r.sigma, r.freqs)]
@@ -903,7 +914,8 @@ def main(argv=None):
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-per-m", action="store_true", help="skip the M = 10 / 50 lines of the sweep")
-    ap.add_argument("--autotune", action="store_true", help="measure and install tuned kernel shapes before timing")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="time the built-in kernel shapes (default: measure and install tuned shapes first)")
     ap.add_argument("--configs", nargs="?", const="all", default=None,
                     choices=["all", "batch", "accum", "shared", "drift", "multi", "entropy"],
                     help="report every workload (one JSON line each) instead, or one section of them")

@@ -18,7 +18,7 @@
  *     A_m  = sum_{i in bin m} x_i * w_i         (numerator sums)
  *     B_m  = sum_{i in bin m} w_i               (denominator sums)
  *     S(f) = sum_m A_m^2 / (B_m + 1/alpha^2)
- *   Readings where the paper is silent (each also listed in the design doc):
+ *   Readings where the paper is silent or inconsistent:
  *     - the denominator is Eq. 1's B_m + 1/alpha^2 (not the appendix listing's
  *       factor-2 form); inv_alpha2 = 1/alpha^2 is a parameter (0 = the paper's
  *       practice of neglecting the term);

@@ -31,8 +31,9 @@ __device__ __forceinline__ float entropy_from_counts_sum(float sum_clogc, float 
 // frac(t_i df) as 64-bit fixed point; where the block's frequencies lie on the
 // linear grid (the tile kernels' bound on the phase error) frequency j of the
 // block has phase P_i + j D_i (mod 2^64), as in the periodogram kernels, else
-// the exact anchor at its own frequency. Two observations per iteration, all
-// counts loaded before any store (a shared bin counts both).
+// the exact anchor at its own frequency. One observation per iteration: its R
+// counts (in disjoint slots) are all loaded before any store, and the next
+// observation's staged data is loaded before them.
 template <int R>
 __global__ void __launch_bounds__(kEntThreads) entropy_dense_kernel(const double* t, int64_t n, const double* freqs,
                                                                     int64_t nfreq, int M, float* H_out) {
@@ -76,44 +77,39 @@ __global__ void __launch_bounds__(kEntThreads) entropy_dense_kernel(const double
                    : make_ulonglong2((unsigned long long)__double_as_longlong(ti), 0ull);
     }
     __syncthreads();
-    // count slots of one observation for the thread's R frequencies
-    auto slots = [&](const ulonglong2 pd, int (&sl)[R]) {
-      if (lin) {
+    unsigned* const mine = cnt + tid;  // this thread's column of the [r][m][thread] counts
+    if (lin) {
+      ulonglong2 pd = sPD[0];
+#pragma unroll 2
+      for (int i = 0; i < c; ++i) {
+        const ulonglong2 pdn = sPD[(i + 1 < c) ? i + 1 : i];
         unsigned long long phi = pd.x + (unsigned long long)j0 * pd.y;
+        unsigned* sl[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-          sl[r] = r * MT + (int)bin_of_phase(phi, (unsigned)M) * kEntThreads + tid;
+          sl[r] = mine + r * MT + bin_of_phase(phi, (unsigned)M) * kEntThreads;
           phi += pd.y;
         }
-      } else {
-        const double ti = __longlong_as_double((long long)pd.x);
+        unsigned v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = *sl[r];
+#pragma unroll
+        for (int r = 0; r < R; ++r) *sl[r] = v[r] + 1u;
+        pd = pdn;
+      }
+    } else {
+      for (int i = 0; i < c; ++i) {
+        const double ti = __longlong_as_double((long long)sPD[i].x);
+        unsigned* sl[R];
 #pragma unroll
         for (int r = 0; r < R; ++r)
-          sl[r] = r * MT + (int)bin_of_phase(phase_fixed64(ti, fk[r]), (unsigned)M) * kEntThreads + tid;
-      }
-    };
-    int i = 0;
-    for (; i + 1 < c; i += 2) {
-      int sa[R], sb[R];
-      slots(sPD[i], sa);
-      slots(sPD[i + 1], sb);
-      unsigned va[R], vb[R];
+          sl[r] = mine + r * MT + bin_of_phase(phase_fixed64(ti, fk[r]), (unsigned)M) * kEntThreads;
+        unsigned v[R];
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        va[r] = cnt[sa[r]];
-        vb[r] = cnt[sb[r]];
-      }
+        for (int r = 0; r < R; ++r) v[r] = *sl[r];
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        cnt[sa[r]] = va[r] + 1u;
-        cnt[sb[r]] = (sa[r] == sb[r] ? va[r] + 1u : vb[r]) + 1u;
+        for (int r = 0; r < R; ++r) *sl[r] = v[r] + 1u;
       }
-    }
-    if (i < c) {
-      int sa[R];
-      slots(sPD[i], sa);
-#pragma unroll
-      for (int r = 0; r < R; ++r) cnt[sa[r]] += 1u;
     }
   }
 #pragma unroll
@@ -187,11 +183,12 @@ __global__ void __launch_bounds__(kPeakWarps * 32) entropy_peaks_kernel(const in
 cudaError_t launch_entropy_dense(const double* t, int64_t n, const double* freqs, int64_t nfreq, int M, float* H_out,
                                  cudaStream_t st) {
   if (nfreq <= 0) return cudaSuccess;
-  // two frequencies per thread while the counts stay small (M <= 96: 96 KB per
-  // block at most), one beyond
-  const int R = M <= 96 ? 2 : 1;
-  const void* fn = R == 2 ? reinterpret_cast<const void*>(&entropy_dense_kernel<2>)
-                          : reinterpret_cast<const void*>(&entropy_dense_kernel<1>);
+  // frequencies per thread: as many as keep the counts of a block within
+  // 48 KB (four blocks per SM), one beyond M = 96
+  const int R = M <= 24 ? 4 : (M <= 96 ? 2 : 1);
+  const void* fn = R == 4   ? reinterpret_cast<const void*>(&entropy_dense_kernel<4>)
+                   : R == 2 ? reinterpret_cast<const void*>(&entropy_dense_kernel<2>)
+                            : reinterpret_cast<const void*>(&entropy_dense_kernel<1>);
   const size_t smem = (size_t)kEntChunk * 16 + (size_t)R * M * kEntThreads * 4;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
