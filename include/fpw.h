@@ -88,6 +88,9 @@ typedef struct fpw_params {
   int freqs_per_thread; /* 0 = tuned; else 1, 2, 4 or 8 */
   int obs_chunk;        /* 0 = tuned; else observations staged in shared memory per pass (>= 32) */
   int use_graph;        /* 1 = capture the launch sequence in a CUDA graph and replay it on identical calls */
+  int items_per_slot;   /* 0 = tuned (default 8); else the persistent schedule's work items per resident block:
+                           each curve's frequency range is cut into segments of about total cost /
+                           (items_per_slot x resident blocks), longest first (>= 1) */
 } fpw_params;
 
 /* Fill *p with the defaults listed above. */
@@ -297,15 +300,16 @@ FPW_API int fpw_periodogram_batch_noalloc(void* stream, const fpw_params* params
                                           int M, int k, int32_t* topk_idx, float* topk_S);
 
 /* Tuned kernel shapes. Adds a shape -- threads per block (multiple of 32,
- * 32..512), frequencies per thread (1, 2, 4 or 8) and observations per pass
- * (0 = largest that keeps two blocks per SM) -- used for batched and single
+ * 32..512), frequencies per thread (1, 2, 4 or 8), observations per pass
+ * (0 = largest that keeps two blocks per SM) and work items per resident block
+ * (0 = 8; see fpw_params.items_per_slot) -- used for batched and single
  * calls whose bin count lies in [M_lo, M_hi] and whose observation-weighted
  * mean curve size lies in [n_lo, n_hi). Later entries take precedence; explicit
  * fpw_params fields override the table. The autotuner
  * (paper_2502_00243_gb300/autotune.py) measures candidates and fills it.
  * Errors: FPW_EINVAL for an empty range or an invalid shape. */
 FPW_API int fpw_ctx_set_shape(fpw_ctx* ctx, int M_lo, int M_hi, int64_t n_lo, int64_t n_hi, int threads,
-                              int freqs_per_thread, int obs_chunk);
+                              int freqs_per_thread, int obs_chunk, int items_per_slot);
 FPW_API int fpw_ctx_clear_shapes(fpw_ctx* ctx);
 
 /* The tile-kernel shape of the context's most recent batched or single-curve
@@ -339,7 +343,8 @@ FPW_API int fpw_ctx_kernel_time(fpw_ctx* ctx, double* ms, int64_t* launches);
 FPW_API const char* fpw_strerror(int status);
 
 /* Library ABI version (increments on incompatible changes; 2: fpw_debug_bins
- * replaced by fpw_periodogram_batch_bins). */
+ * replaced by fpw_periodogram_batch_bins, fpw_params.items_per_slot added,
+ * fpw_ctx_set_shape takes items_per_slot). */
 FPW_API int fpw_version(void);
 
 /* Text of the last CUDA runtime error seen by the calling thread (static,

@@ -47,7 +47,8 @@ class FPWError(RuntimeError):
 class fpw_params(ctypes.Structure):
     _fields_ = [("inv_alpha2", ctypes.c_double), ("phase_mode", ctypes.c_int), ("accum", ctypes.c_int),
                 ("K", ctypes.c_int), ("peak_mode", ctypes.c_int), ("threads", ctypes.c_int),
-                ("freqs_per_thread", ctypes.c_int), ("obs_chunk", ctypes.c_int), ("use_graph", ctypes.c_int)]
+                ("freqs_per_thread", ctypes.c_int), ("obs_chunk", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("items_per_slot", ctypes.c_int)]
 
 
 _lock = threading.Lock()
@@ -89,7 +90,7 @@ def lib():
                 "fpw_ctx_set_timing": (ci, [vp, ci]),
                 "fpw_ctx_kernel_time": (ci, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
                 "fpw_periodogram_batch_noalloc": (ci, [vp, P, vp, vp, i64, vp, vp, vp, vp, i64, ci, ci, vp, vp]),
-                "fpw_ctx_set_shape": (ci, [vp, ci, ci, i64, i64, ci, ci, ci]),
+                "fpw_ctx_set_shape": (ci, [vp, ci, ci, i64, i64, ci, ci, ci, ci]),
                 "fpw_ctx_clear_shapes": (ci, [vp]),
                 "fpw_phase_entropy": (ci, [vp, vp, vp, i64, vp, i64, ci, vp]),
                 "fpw_periodogram_shared": (ci, [vp, vp, P, vp, i64, i64, vp, vp, vp, i64, ci, ci, vp, vp, vp]),
@@ -157,9 +158,9 @@ class Context:
         return int(lib().fpw_ctx_status(self.handle))
 
     def set_shape(self, M_lo: int, M_hi: int, n_lo: int, n_hi: int, threads: int, freqs_per_thread: int,
-                  obs_chunk: int = 0) -> None:
-        _check(lib().fpw_ctx_set_shape(self.handle, M_lo, M_hi, n_lo, n_hi, threads, freqs_per_thread, obs_chunk),
-               "fpw_ctx_set_shape")
+                  obs_chunk: int = 0, items_per_slot: int = 0) -> None:
+        _check(lib().fpw_ctx_set_shape(self.handle, M_lo, M_hi, n_lo, n_hi, threads, freqs_per_thread, obs_chunk,
+                                       items_per_slot), "fpw_ctx_set_shape")
 
     def clear_shapes(self) -> None:
         _check(lib().fpw_ctx_clear_shapes(self.handle), "fpw_ctx_clear_shapes")

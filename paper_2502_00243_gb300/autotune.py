@@ -1,10 +1,13 @@
 """Autotuner for the FPW tile kernel's shape.
 
-For each (bin count M, curve-size bucket) it times candidate shapes -- threads
-per block x frequencies per thread -- on synthetic light curves through the C
-ABI (the library's own timing hook: CUDA events around the tile kernel on its
-stream) and installs the fastest in a context's shape table
-(``fpw_ctx_set_shape``). The table can be saved to / loaded from JSON.
+For each (bin count M, curve-size bucket) it times candidate shapes on
+synthetic light curves through the C ABI (the library's own timing hook: CUDA
+events around the tile kernel on its stream) and installs the fastest in a
+context's shape table (``fpw_ctx_set_shape``), in two stages: threads per block
+x frequencies per thread, then, for the best of those, the observations staged
+per pass (which set the blocks per SM) x the work items per resident block
+(the segment size of the persistent schedule's curve-to-block mapping). The
+table can be saved to / loaded from JSON.
 
 Shapes matter because the kernel is bound by the shared-memory pipe: every
 (thread, frequency) slot holds M (A, B) bin pairs, so M and the frequencies
@@ -21,6 +24,7 @@ import numpy as np
 from . import Context, FPWError, fpw_params_default, fpw_periodogram_batch_ex
 
 CANDIDATES = ((128, 8), (128, 4), (128, 2), (128, 1), (256, 4), (256, 2), (256, 1), (64, 8), (64, 4), (192, 2))
+SCHEDULES = ((0, 8), (0, 4), (0, 16), (256, 8), (512, 8))  # (observations per pass, items per resident block)
 DEFAULT_MS = (10, 20, 50)
 DEFAULT_BUCKETS = ((0, 300), (300, 1000), (1000, 1 << 40))
 
@@ -52,13 +56,13 @@ def synthetic_curves(n, ncurves, seed=0):
     return offsets, t, x, sigma
 
 
-def measure(ctx, dev, offsets_h, freqs, M, k, T, R, reps=2):
+def measure(ctx, dev, offsets_h, freqs, M, k, T, R, reps=2, NC=0, items=0):
     """Mean tile-kernel milliseconds for one shape, or None if it does not fit."""
     import torch
     C = offsets_h.shape[0] - 1
     idx = torch.empty(C * k, dtype=torch.int32, device="cuda")
     S = torch.empty(C * k, dtype=torch.float32, device="cuda")
-    p = fpw_params_default(threads=T, freqs_per_thread=R)
+    p = fpw_params_default(threads=T, freqs_per_thread=R, obs_chunk=NC, items_per_slot=items)
     try:
         fpw_periodogram_batch_ex(ctx, None, p, dev[0], offsets_h, dev[1], dev[2], dev[3], freqs, M, k, idx, S)
         torch.cuda.synchronize()
@@ -76,7 +80,7 @@ def measure(ctx, dev, offsets_h, freqs, M, k, T, R, reps=2):
 
 
 def tune(ctx: Context, Ms=DEFAULT_MS, buckets=DEFAULT_BUCKETS, *, nfreq=50_000, evals_per_case=1.5e10, k=5,
-         candidates=CANDIDATES, apply=True, log=None):
+         candidates=CANDIDATES, schedules=SCHEDULES, apply=True, log=None):
     """Measure every candidate shape per (M, bucket); returns the table entries
     (and installs them in ``ctx`` when ``apply``)."""
     import torch
@@ -101,8 +105,19 @@ def tune(ctx: Context, Ms=DEFAULT_MS, buckets=DEFAULT_BUCKETS, *, nfreq=50_000, 
                     best = (T, R, rate)
             if best is None:
                 continue
+            sched = (0, 0, best[2])
+            for NC, items in schedules:
+                ms = measure(ctx, dev, off, freqs, M, k, best[0], best[1], NC=NC, items=items)
+                if ms is None:
+                    continue
+                rate = evals / (ms / 1e3)
+                if log:
+                    log(f"M={M} n={n} T={best[0]} R={best[1]} NC={NC} items={items}: {rate / 1e9:.1f} Geval/s")
+                if rate > sched[2]:
+                    sched = (NC, items, rate)
             e = {"M_lo": m_lo, "M_hi": m_hi, "n_lo": int(b_lo), "n_hi": int(min(b_hi, 1 << 40)), "threads": best[0],
-                 "freqs_per_thread": best[1], "obs_chunk": 0, "geval_s": best[2] / 1e9, "M": M, "n": n}
+                 "freqs_per_thread": best[1], "obs_chunk": sched[0], "items_per_slot": sched[1],
+                 "geval_s": sched[2] / 1e9, "M": M, "n": n}
             entries.append(e)
     if apply:
         install(ctx, entries)
@@ -112,7 +127,7 @@ def tune(ctx: Context, Ms=DEFAULT_MS, buckets=DEFAULT_BUCKETS, *, nfreq=50_000, 
 def install(ctx: Context, entries) -> None:
     for e in entries:
         ctx.set_shape(e["M_lo"], e["M_hi"], e["n_lo"], e["n_hi"], e["threads"], e["freqs_per_thread"],
-                      e.get("obs_chunk", 0))
+                      e.get("obs_chunk", 0), e.get("items_per_slot", 0))
 
 
 def save(entries, path: str) -> None:

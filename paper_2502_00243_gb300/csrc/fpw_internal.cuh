@@ -126,6 +126,7 @@ struct TileShape {
   int R;         // frequencies per thread
   int obs_chunk; // NC
   size_t smem;   // dynamic shared memory bytes
+  int items;     // work items per resident block in the persistent schedule
 };
 
 // ---- launch wrappers (defined in the .cu files) -------------------------

@@ -136,6 +136,7 @@ extern "C" FPW_API int fpw_periodogram_batch_noalloc(void* stream, const fpw_par
   if (p.threads != 0 && (p.threads < 32 || p.threads > 512 || p.threads % 32 != 0)) return FPW_EINVAL;
   if (p.freqs_per_thread != 0 && !tile_supported_R(p.freqs_per_thread)) return FPW_EINVAL;
   if (p.obs_chunk != 0 && p.obs_chunk < 32) return FPW_EINVAL;
+  if (p.items_per_slot < 0) return FPW_EINVAL;  // one item per curve here; the value is not used
   (void)cudaGetLastError();
 
   int dev = 0;

@@ -101,7 +101,7 @@ struct Plan {
 struct ShapeEntry {
   int M_lo, M_hi;
   int64_t n_lo, n_hi;
-  int T, R, NC;
+  int T, R, NC, items;
 };
 
 struct GraphEntry {
@@ -176,6 +176,7 @@ bool valid_params(const fpw_params& p) {
   if (p.threads != 0 && (p.threads < 32 || p.threads > 512 || p.threads % 32 != 0)) return false;
   if (p.freqs_per_thread != 0 && !tile_supported_R(p.freqs_per_thread)) return false;
   if (p.obs_chunk != 0 && p.obs_chunk < 32) return false;
+  if (p.items_per_slot < 0) return false;
   return true;
 }
 
@@ -192,7 +193,7 @@ bool valid_params(const fpw_params& p) {
 int choose_shape(fpw_ctx* ctx, const fpw_params& p, int M, int k, int64_t max_n, int64_t n_typ, int ngroups,
                  TileShape& out) {
   const bool wide = p.accum != FPW_ACCUM_FP32;  // 16-byte bins
-  int T = 128, R = 4, NC = 0;
+  int T = 128, R = 4, NC = 0, items = 8;
   if (wide)
     R = 2;
   else if (M <= 12)
@@ -214,8 +215,10 @@ int choose_shape(fpw_ctx* ctx, const fpw_params& p, int M, int k, int64_t max_n,
       T = e.T;
       R = e.R;
       NC = e.NC;
+      items = e.items ? e.items : 8;
     }
   if (p.threads) T = p.threads;
+  if (p.items_per_slot) items = p.items_per_slot;
   if (p.freqs_per_thread) R = p.freqs_per_thread;
   if (p.obs_chunk) NC = p.obs_chunk;
   const bool fixedT = p.threads != 0;
@@ -251,11 +254,12 @@ int choose_shape(fpw_ctx* ctx, const fpw_params& p, int M, int k, int64_t max_n,
   out.R = R;
   out.obs_chunk = NC;
   out.smem = smem;
+  out.items = items;
   return FPW_OK;
 }
 
 // Work items: each curve's frequency range split into segments of whole tiles
-// so that every resident block gets several items (load balance), sorted by
+// so that every resident block gets about sh.items items (load balance), sorted by
 // cost (observations x frequencies) descending; candidate rows per curve in
 // curve order. The tables are uploaded from a pinned copy, ordered on `st`.
 Plan* build_plan(fpw_ctx* ctx, const int64_t* off, int64_t C, int64_t F, const TileShape& sh, int blocks_per_sm,
@@ -266,7 +270,7 @@ Plan* build_plan(fpw_ctx* ctx, const int64_t* off, int64_t C, int64_t F, const T
   const int resident = std::max(1, blocks_per_sm * ctx->nsm);
   double total = 0.0;
   for (int64_t c = 0; c < C; ++c) total += (double)(off[c + 1] - off[c] + 32) * (double)F;
-  const double target = std::max(total / (8.0 * resident), 32.0 * (double)Wown * 16.0);
+  const double target = std::max(total / ((double)sh.items * resident), 32.0 * (double)Wown * 16.0);
   std::vector<WorkItem> items;
   std::vector<double> cost;
   std::vector<int32_t> base((size_t)C + 1, 0);
@@ -331,6 +335,7 @@ Plan* get_plan(fpw_ctx* ctx, const int64_t* off, int64_t C, int64_t F, const Til
   key = mix(key, sh.R);
   key = mix(key, sh.obs_chunk);
   key = mix(key, sh.smem);
+  key = mix(key, sh.items);
   key = mix(key, blocks_per_sm);
   for (Plan* p : ctx->plans)
     if (p->key == key) {
@@ -807,12 +812,12 @@ int fpw_ctx_destroy(fpw_ctx* ctx) {
 }
 
 int fpw_ctx_set_shape(fpw_ctx* ctx, int M_lo, int M_hi, int64_t n_lo, int64_t n_hi, int threads, int freqs_per_thread,
-                      int obs_chunk) {
+                      int obs_chunk, int items_per_slot) {
   if (!ctx || M_lo < 1 || M_hi < M_lo || n_lo < 0 || n_hi <= n_lo) return FPW_EINVAL;
   if (threads < 32 || threads > 512 || threads % 32 != 0 || !tile_supported_R(freqs_per_thread)) return FPW_EINVAL;
-  if (obs_chunk != 0 && obs_chunk < 32) return FPW_EINVAL;
+  if ((obs_chunk != 0 && obs_chunk < 32) || items_per_slot < 0) return FPW_EINVAL;
   std::lock_guard<std::mutex> lk(ctx->mu);
-  ShapeEntry e{M_lo, M_hi, n_lo, n_hi, threads, freqs_per_thread, obs_chunk};
+  ShapeEntry e{M_lo, M_hi, n_lo, n_hi, threads, freqs_per_thread, obs_chunk, items_per_slot};
   ctx->shapes.push_back(e);
   return FPW_OK;
 }

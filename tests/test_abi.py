@@ -40,9 +40,9 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_params_layout_and_defaults(lib):
     p = G.fpw_params_default()
-    assert ctypes.sizeof(p) == 40
+    assert ctypes.sizeof(p) == 48
     assert (p.inv_alpha2, p.phase_mode, p.accum, p.K, p.peak_mode, p.use_graph) == (0.0, 0, 0, 256, 0, 0)
-    assert (p.threads, p.freqs_per_thread, p.obs_chunk) == (0, 0, 0)
+    assert (p.threads, p.freqs_per_thread, p.obs_chunk, p.items_per_slot) == (0, 0, 0, 0)
 
 
 def test_host_only_calls(lib):

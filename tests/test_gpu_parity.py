@@ -303,3 +303,22 @@ def test_plain_fp64_batch_form(ctx):
     for ci in range(w.ncurves):
         np.testing.assert_array_equal(idx[ci], o_idx[ci])
         np.testing.assert_array_equal(Sk[ci], o_S[ci].astype(np.float32))
+
+
+# ------------------------------------------------------------------ schedule: work items per resident block
+def test_work_item_split_leaves_every_value_unchanged(ctx):
+    """Tile anchors sit at q (W - 2) - 1 whatever the item boundaries, so the
+    segment size of the persistent schedule changes no S value and no peak."""
+    w = L.ragged(80, [2900, 35, 1200, 64, 700, 0, 2100], 20_000, M=20, k=6)
+    d = to_dev(w)
+    ref = run_batch(ctx, w, d=d, dense=True)
+    assert ref[3] == 0
+    for items in (1, 3, 64):
+        got = run_batch(ctx, w, d=d, dense=True, params=P(items_per_slot=items))
+        assert got[3] == 0
+        np.testing.assert_array_equal(got[2], ref[2])
+        np.testing.assert_array_equal(got[0], ref[0])
+        np.testing.assert_array_equal(got[1], ref[1])
+    with pytest.raises(G.FPWError) as ei:
+        run_batch(ctx, w, d=d, params=P(items_per_slot=-1))
+    assert ei.value.code == G.FPW_EINVAL

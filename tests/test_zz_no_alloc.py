@@ -99,6 +99,26 @@ def test_noalloc_rejects_malformed_device_offsets(G):
     _noalloc(G, w, d, None)  # and the next call runs
 
 
+def test_noalloc_compensated_sums_match_the_batched_call(G):
+    w = L.ragged(34, [800, 1500, 45, 2200], 5000, M=20, k=5)
+    d = to_dev(w)
+    p = G.fpw_params_default(accum=G.FPW_ACCUM_FP32_COMP)
+    ctx = G.Context(0)
+    ref_idx, ref_S, _, st = run_batch(ctx, w, d=d, params=p)
+    assert st == 0
+    ctx.close()
+    C, k = w.ncurves, w.k
+    idx = torch.full((C * k,), -7, dtype=torch.int32, device="cuda")
+    S = torch.full((C * k,), -7.0, dtype=torch.float32, device="cuda")
+    G.fpw_periodogram_batch_noalloc(None, p, d["offsets"], w.offsets, d["t"], d["x"], d["sigma"], d["freqs"], w.M, k,
+                                    idx, S)
+    idx, S = idx.cpu().numpy().reshape(C, k), S.cpu().numpy().reshape(C, k)
+    for c in range(C):
+        t, x, s = w.curve(c)
+        check_topk(idx[c], S[c], ref_idx[c], ref_S[c].astype(np.float64), rel=1e-6, abs_tol=1e-9 * s_bound(x, s),
+                   what=f"noalloc compensated curve {c}")
+
+
 def test_noalloc_rejects_inputs_beyond_its_scratch(G):
     n = 5_000_000  # 8 B of weights per observation exceeds the 32 MiB array
     off = np.array([0, n], dtype=np.int64)
