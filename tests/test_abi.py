@@ -87,3 +87,21 @@ def test_oracle_and_library_are_independent():
             txt = open(f).read()
             assert not re.search(r"^\s*(import|from)\s+paper_2502_00243_gb300", txt, re.M), f
             assert "#include \"" not in txt and "libfpw" not in txt, f
+
+
+def _declared_arity():
+    """Parameter count of every FPW_API function in the header."""
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    out = {}
+    for m in re.finditer(r"FPW_API\s+[\w\s\*]+?\b(fpw_\w+)\s*\(([^)]*)\)", text):
+        args = m.group(2).strip()
+        out[m.group(1)] = 0 if args in ("", "void") else args.count(",") + 1
+    return out
+
+
+def test_binding_argument_counts_match_the_header(lib):
+    arity = _declared_arity()
+    assert set(arity) == set(G.EXPORTED)
+    for name, n in arity.items():
+        argtypes = getattr(lib, name).argtypes
+        assert argtypes is not None and len(argtypes) == n, f"{name}: header {n} args, binding {argtypes}"
