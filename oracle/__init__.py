@@ -29,6 +29,10 @@ Functions and the passages they follow:
   their times, bins computed once per frequency.
 * :func:`fpw_drift` (``drift.py``, numpy) -- Appendix A.1-A.2: the statistic with
   a polynomial baseline drift marginalised, formed densely.
+
+``sanitize_driver.c`` calls every C entry point on seeded inputs and edge cases;
+the tests build it with the C source under AddressSanitizer and
+UndefinedBehaviorSanitizer.
 """
 from __future__ import annotations
 

@@ -13,6 +13,10 @@ peak finder; each part reports its k best owned peaks, and the parts' lists
 merge by S descending, ties to the lower frequency index (Section 3.5's
 peaks, with the library's ranking).
 
+Long runs can be checkpointed: `run_chunked` processes a batch chunk by chunk,
+saves each finished chunk's top-k and, rerun after an interruption, skips the
+chunks already saved.
+
 The compute step is a callable so that the partition and merge logic can be
 exercised without a GPU; by default it is the library's batched call.
 """
@@ -136,3 +140,37 @@ def curve_topk_split(compute, t, x, sigma, freqs, k: int, rank: int = 0, world: 
         mine = owned_topk(np.asarray(idx)[0], np.asarray(S)[0], a, lo, hi, k)
     got = _gather(dist, mine, world)
     return merge_topk(got, k)
+
+
+def run_chunked(compute, offsets, t, x, sigma, freqs, k: int, chunk_curves: int, state_dir=None):
+    """Per-curve top-k of a batch processed in chunks of `chunk_curves` curves.
+
+    With `state_dir`, each finished chunk's top-k is saved there
+    (``chunk_<first curve>_<count>.npz``, written to a temporary name and
+    renamed, so a file is either complete or absent), and a rerun loads the
+    chunks already saved instead of recomputing them: a long run interrupted
+    at any point resumes where it stopped. Returns ``(idx [C, k], S [C, k])``
+    in curve order."""
+    import os
+
+    offsets = np.asarray(offsets, dtype=np.int64)
+    C = len(offsets) - 1
+    out_i = np.full((C, k), -1, dtype=np.int32)
+    out_s = np.full((C, k), np.nan, dtype=np.float32)
+    if state_dir is not None:
+        os.makedirs(state_dir, exist_ok=True)
+    for c0 in range(0, C, max(1, int(chunk_curves))):
+        ids = np.arange(c0, min(C, c0 + int(chunk_curves)), dtype=np.int64)
+        path = None if state_dir is None else os.path.join(state_dir, f"chunk_{c0}_{len(ids)}.npz")
+        if path is not None and os.path.exists(path):
+            with np.load(path) as z:
+                out_i[ids], out_s[ids] = z["idx"], z["S"]
+            continue
+        o, tt, xx, ss = subset(offsets, t, x, sigma, ids)
+        idx, S = compute(o, tt, xx, ss, freqs, k)
+        out_i[ids], out_s[ids] = idx, S
+        if path is not None:
+            tmp = path + ".tmp.npz"
+            np.savez(tmp, idx=np.asarray(idx, dtype=np.int32), S=np.asarray(S, dtype=np.float32))
+            os.replace(tmp, path)
+    return out_i, out_s

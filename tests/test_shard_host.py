@@ -83,3 +83,30 @@ def test_frequency_parts_own_every_frequency_once_with_halos():
 def test_merge_ranks_by_S_then_lower_index():
     idx, S = shard.merge_topk([[(7, 2.0), (3, 1.0)], [(5, 2.0), (9, 0.5)]], 5)
     assert list(idx) == [5, 7, 3, 9, -1] and np.isnan(S[4])
+
+
+def test_chunked_run_resumes_after_an_interruption(tmp_path):
+    w = L.ragged(7, [300, 0, 1200, 50, 800, 999, 31, 450, 2000], 1500, M=10, k=4)
+    full_i, full_s = shard.run_chunked(oracle_compute(10), w.offsets, w.t, w.x, w.sigma, w.freqs, 4, 100)
+    calls = []
+
+    def flaky(offsets, t, x, sigma, freqs, k):
+        if len(calls) == 2:
+            raise RuntimeError("interrupted")
+        calls.append(len(offsets) - 1)
+        return oracle_compute(10)(offsets, t, x, sigma, freqs, k)
+
+    with pytest.raises(RuntimeError):
+        shard.run_chunked(flaky, w.offsets, w.t, w.x, w.sigma, w.freqs, 4, 2, state_dir=str(tmp_path))
+    assert calls == [2, 2] and len(list(tmp_path.glob("chunk_*.npz"))) == 2
+    done = []
+
+    def counted(offsets, t, x, sigma, freqs, k):
+        done.append(len(offsets) - 1)
+        return oracle_compute(10)(offsets, t, x, sigma, freqs, k)
+
+    ri, rs = shard.run_chunked(counted, w.offsets, w.t, w.x, w.sigma, w.freqs, 4, 2, state_dir=str(tmp_path))
+    assert done == [2, 2, 1]  # the two saved chunks are not recomputed
+    np.testing.assert_array_equal(ri, full_i)
+    np.testing.assert_array_equal(rs, full_s)
+    assert not list(tmp_path.glob("*.tmp.npz"))
