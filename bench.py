@@ -772,7 +772,7 @@ def run_configs_entropy(ctx, peak):
     w = L.make("single_ztf")
     t, fr = torch.from_numpy(w.t).cuda(), torch.from_numpy(w.freqs).cuda()
     H = torch.empty(w.nfreq, dtype=torch.float32, device="cuda")
-    for M in (20, 50):
+    for M in (10, 20, 50):
         G.fpw_phase_entropy(ctx, None, t, fr, M, H)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -163,8 +163,9 @@ FPW_API int fpw_periodogram_batch_ex(fpw_ctx* ctx, void* stream, const fpw_param
  *   topk_offset: device int32[ncurves * ngroups * k], the offset o of each peak (-1 if none)
  *   topk_S:      device float32[ncurves * ngroups * k]
  *   S_out:       optional device float64[ncurves * ngroups * nfreq], S_g(f) per curve and group
- * Other arguments as fpw_periodogram_batch_ex. FP32 sums only (FPW_ENOTSUP
- * otherwise); nfreq < 2^25 when k > 0. Stream-ordered. */
+ * Other arguments as fpw_periodogram_batch_ex. FP32 sums only and at most 256
+ * threads per block (FPW_ENOTSUP otherwise); nfreq < 2^25 when k > 0.
+ * Stream-ordered. */
 FPW_API int fpw_periodogram_batch_multi(fpw_ctx* ctx, void* stream, const fpw_params* params, const int64_t* offsets,
                                         const int64_t* offsets_host, int64_t ncurves, const double* t,
                                         const double* x, const double* sigma, const double* freqs, int64_t nfreq,

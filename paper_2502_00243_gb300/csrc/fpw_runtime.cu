@@ -217,6 +217,7 @@ int choose_shape(fpw_ctx* ctx, const fpw_params& p, int M, int k, int64_t max_n,
       NC = e.NC;
       items = e.items ? e.items : 8;
     }
+  if (ngroups > 0 && T > 256) T = 256;  // the several-M kernel's launch bound (table entries may be wider)
   if (p.threads) T = p.threads;
   if (p.items_per_slot) items = p.items_per_slot;
   if (p.freqs_per_thread) R = p.freqs_per_thread;
@@ -919,6 +920,7 @@ int fpw_periodogram_batch_multi(fpw_ctx* ctx, void* stream, const fpw_params* pa
   if (params) p = *params;
   if (!valid_params(p)) return FPW_EINVAL;
   if (p.accum != FPW_ACCUM_FP32 || p.phase_mode == FPW_PHASE_FP64) return FPW_ENOTSUP;
+  if (p.threads > 256) return FPW_ENOTSUP;  // the several-M kernel's launch bound
   DeviceGuard g(ctx->device);
   if (!g.ok) return FPW_ECUDA;
   std::lock_guard<std::mutex> lk(ctx->mu);

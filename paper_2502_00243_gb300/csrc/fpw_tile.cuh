@@ -359,12 +359,12 @@ __device__ __forceinline__ void accumulate_tile(const TileArgs& args, const Bloc
       // is loaded before this one's bin stores (the compiler cannot move it
       // there itself: both are shared memory), so the broadcast-load latency
       // overlaps the bin updates.
-      if (R == 2) {
-        // Software-pipelined (measured faster only at R = 2, where the phase ->
-        // bin -> offset chain is a larger share of each iteration): the bins
-        // of observation i + 1 are computed while observation i's bin loads
-        // are in flight, from staged data loaded one iteration earlier. Same
-        // adds in the same order as the loop below.
+      if (R <= 2) {
+        // Software-pipelined (measured faster at R <= 2, where the phase ->
+        // bin -> offset chain is a larger share of each iteration; slower at
+        // R = 4): the bins of observation i + 1 are computed while observation
+        // i's bin loads are in flight, from staged data loaded one iteration
+        // earlier. Same adds in the same order as the loop below.
         unsigned m[R];
         {
           const ulonglong2 p0 = sPD[0];
@@ -656,9 +656,14 @@ __global__ void __launch_bounds__(512) tile_kernel(const TileArgs args) {
 // Several M from one M_max pass (Section 3.4): the kernel accumulates M_max
 // bins; for each requested group g (M = M_max / g) it reports, per frequency,
 // the largest S over the g bin offsets and that offset (ranking key
-// (k << 6) | offset). FP32 sums.
+// (k << 6) | offset). FP32 sums. At most 256 threads per block (the host
+// rejects more): with that bound the compiler keeps the combination's
+// registers (72-114) instead of spilling them, which it did at 40 registers
+// under a 512-thread bound.
+constexpr int kMultiMaxThreads = 256;
+
 template <int R, int PHASE>
-__global__ void __launch_bounds__(512) tile_kernel_multi(const TileArgs args) {
+__global__ void __launch_bounds__(kMultiMaxThreads, 2) tile_kernel_multi(const TileArgs args) {
   using P = AccF32;
   using A = float;
   using A2 = float2;

@@ -24,7 +24,7 @@ def G():
     return G_
 
 
-@pytest.mark.parametrize("M", [4, 20, 50])
+@pytest.mark.parametrize("M", [4, 10, 20, 50])
 def test_dense_phase_entropy(G, M):
     w = L.make("single_ztf", nfreq=40_000)
     t, _, _ = w.curve(0)

@@ -104,3 +104,27 @@ def test_multi_m_rejects_bad_groups(G):
         run_multi(G, ctx, w, 20, [2], 2, params=G.fpw_params_default(accum=1))
     assert ei.value.code == G.FPW_ENOTSUP
     ctx.close()
+
+
+def test_multi_m_thread_bound(G):
+    """The several-M kernel takes at most 256 threads per block: explicit wider
+    blocks are refused, and a wider shape-table entry is capped, with results
+    equal to the default shape's within rounding of the summation order."""
+    w = L.ragged(77, [600, 1300, 50], 2500, M=20, k=5)
+    ctx = G.Context(0)
+    with pytest.raises(G.FPWError) as ei:
+        run_multi(G, ctx, w, 20, [1, 2], 5, params=G.fpw_params_default(threads=512))
+    assert ei.value.code == G.FPW_ENOTSUP
+    ref = run_multi(G, ctx, w, 20, [1, 2], 5)
+    ctx.set_shape(1, 1000, 0, 1 << 40, 512, 1)
+    got = run_multi(G, ctx, w, 20, [1, 2], 5)
+    assert ctx.last_shape()[0] == 256
+    for c in range(w.ncurves):
+        t, x, s = w.curve(c)
+        bound = s_bound(x, s)
+        near = oracle.min_edge(t, w.freqs, 20) <= 1e-9  # other tiles, other anchors: edge pairs may move
+        for q in range(2):
+            assert_S_close(got[3][c, q], ref[3][c, q], bound, rel=1e-5, absf=1e-7, mask=~near,
+                           what=f"capped shape curve {c}")
+    ctx.clear_shapes()
+    ctx.close()
