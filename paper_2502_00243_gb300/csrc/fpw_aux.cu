@@ -127,6 +127,90 @@ __global__ void merge_kernel(const MergeArgs a) {
   }
 }
 
+// The same selection with one block per curve, for curves with many candidate
+// rows (one long curve split into thousands of work items): each round every
+// thread scans a slice of the rows and the block reduces the per-warp bests,
+// instead of one warp scanning every row k times.
+constexpr int kMergeBlock = 256;
+
+__global__ void __launch_bounds__(kMergeBlock) merge_block_kernel(const MergeArgs a) {
+  __shared__ double ws[kMergeBlock / 32];
+  __shared__ int wi[kMergeBlock / 32];
+  __shared__ int wp[kMergeBlock / 32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const bool grid_bad = (*a.status & kStatusGrid) != 0u;
+  const int64_t stride = a.out_stride > 0 ? a.out_stride : a.k;
+  for (int64_t c = blockIdx.x; c < a.ncurves; c += gridDim.x) {
+    int32_t* oi = a.topk_idx + c * stride;
+    float* os = a.topk_S + c * stride;
+    int32_t* oo = a.topk_off ? a.topk_off + c * stride : nullptr;
+    if (grid_bad || a.curve_bad[c]) {
+      for (int q = tid; q < a.k; q += kMergeBlock) {
+        oi[q] = -1;
+        os[q] = __int_as_float(0x7fc00000);
+        if (oo) oo[q] = -1;
+      }
+      continue;
+    }
+    const int64_t e0 = (int64_t)a.cand_base[c] * a.k, e1 = (int64_t)a.cand_base[c + 1] * a.k;
+    double ps = INFINITY;
+    int pi = -1;
+    for (int q = 0; q < a.k; ++q) {
+      double bs = -INFINITY;
+      int bi = -1, bp = -1;
+      for (int64_t e = e0 + tid; e < e1; e += kMergeBlock) {
+        const int i = a.cand_idx[e];
+        if (i < 0) continue;
+        const double s = a.cand_S[e];
+        const bool after_prev = (q == 0) || ranks_before(ps, pi, s, i);
+        if (after_prev && (bp < 0 || ranks_before(s, i, bs, bi))) {
+          bs = s;
+          bi = i;
+          bp = 1;
+        }
+      }
+      warp_best(bs, bi, bp);
+      if (lane == 0) {
+        ws[warp] = bs;
+        wi[warp] = bi;
+        wp[warp] = bp;
+      }
+      __syncthreads();
+      if (warp == 0) {
+        bs = lane < kMergeBlock / 32 ? ws[lane] : -INFINITY;
+        bi = lane < kMergeBlock / 32 ? wi[lane] : -1;
+        bp = lane < kMergeBlock / 32 ? wp[lane] : -1;
+        warp_best(bs, bi, bp);
+        if (lane == 0) {
+          if (oo) {
+            oi[q] = (bp >= 0) ? (bi >> 6) : -1;
+            oo[q] = (bp >= 0) ? (bi & 63) : -1;
+          } else {
+            oi[q] = (bp >= 0) ? bi : -1;
+          }
+          os[q] = (bp >= 0) ? (float)bs : __int_as_float(0x7fc00000);
+          ws[0] = bs;
+          wi[0] = bi;
+          wp[0] = bp;
+        }
+      }
+      __syncthreads();
+      ps = ws[0];
+      pi = wi[0];
+      const bool none = wp[0] < 0;
+      __syncthreads();
+      if (none) {
+        for (int r = q + 1 + tid; r < a.k; r += kMergeBlock) {
+          oi[r] = -1;
+          os[r] = __int_as_float(0x7fc00000);
+          if (oo) oo[r] = -1;
+        }
+        break;
+      }
+    }
+  }
+}
+
 // Plain binary64 form. One thread per trial frequency; observations staged in
 // shared memory in chunks; per-thread bins [m][thread] as {A, B} binary64.
 // DUMP: also writes the bin of every (observation, frequency) in the window.
@@ -287,6 +371,11 @@ cudaError_t launch_prep(const PrepArgs& a, cudaStream_t st) {
 
 cudaError_t launch_merge(const MergeArgs& a, cudaStream_t st) {
   if (a.ncurves <= 0 || a.k <= 0) return cudaSuccess;
+  if ((int64_t)a.max_rows * a.k > 512) {  // long curves: a block per curve
+    const int64_t blocks = a.ncurves < 65535 ? a.ncurves : 65535;
+    merge_block_kernel<<<(unsigned)blocks, kMergeBlock, 0, st>>>(a);
+    return cudaGetLastError();
+  }
   int blocks = (int)((a.ncurves + 7) / 8);
   blocks = blocks > 65535 ? 65535 : blocks;
   merge_kernel<<<blocks, 256, 0, st>>>(a);

@@ -88,6 +88,7 @@ struct MergeArgs {
   float* topk_S;
   int out_stride;
   int32_t* topk_off;         // several-M: receives key & 63 (the bin offset); topk_idx then gets key >> 6
+  int max_rows;              // most candidate rows of one curve (0: unknown); many rows take a block per curve
 };
 
 struct PlainArgs {           // binary64 plain form, one curve

@@ -91,6 +91,7 @@ struct Plan {
   int grid = 0;
   int nitems = 0;
   int nslots = 0;
+  int max_rows = 0;  // most candidate rows (work items) of one curve
   DevBuf items, cand_base;
   void* host_stage = nullptr;  // pinned copy of items + cand_base, the source of the asynchronous upload
   uint64_t use = 0;
@@ -307,6 +308,7 @@ Plan* build_plan(fpw_ctx* ctx, const int64_t* off, int64_t C, int64_t F, const T
   pl->shape = sh;
   pl->nitems = (int)sorted.size();
   pl->nslots = base[C];
+  for (int64_t c = 0; c < C; ++c) pl->max_rows = std::max(pl->max_rows, base[c + 1] - base[c]);
   pl->grid = std::max(1, std::min(resident, pl->nitems));
   const size_t ib = sorted.size() * sizeof(WorkItem), bb = base.size() * sizeof(int32_t);
   cudaError_t e = ensure(pl->items, ib);
@@ -473,6 +475,7 @@ int enqueue_tile_path(fpw_ctx* ctx, const BatchCall& b, Plan* pl, unsigned* word
       ma.topk_S = b.topk_S + (int64_t)q * b.k;
       ma.out_stride = ng * b.k;
       ma.topk_off = b.ngroups > 0 ? b.topk_off + (int64_t)q * b.k : nullptr;
+      ma.max_rows = pl->max_rows;
       FPW_CK(launch_merge(ma, st));
     }
   }

@@ -128,3 +128,38 @@ def test_multi_m_thread_bound(G):
                            what=f"capped shape curve {c}")
     ctx.clear_shapes()
     ctx.close()
+
+
+def test_long_curve_peaks_merged_by_a_block(G):
+    """A curve whose grid splits into hundreds of work items (its candidate rows
+    are merged by a whole block instead of one warp), next to short ones, in the
+    single-M call and in the several-M call (peaks with their offsets)."""
+    w = L.ragged(78, [1500, 40, 600], 200_000, M=12, k=7)
+    ctx = G.Context(0)
+    d = to_dev(w)
+    idx = torch.empty(w.ncurves * 7, dtype=torch.int32, device="cuda")
+    S = torch.empty(w.ncurves * 7, dtype=torch.float32, device="cuda")
+    G.fpw_periodogram_batch_ex(ctx, None, None, d["offsets"], w.offsets, d["t"], d["x"], d["sigma"], d["freqs"], 12,
+                               7, idx, S)
+    torch.cuda.synchronize()
+    assert ctx.status() == 0
+    idx, S = idx.cpu().numpy().reshape(-1, 7), S.cpu().numpy().reshape(-1, 7)
+    S_or, o_idx, o_S = oracle.fpw_batch(w.offsets, w.t, w.x, w.sigma, w.freqs, 12, k=11)
+    for c in range(w.ncurves):
+        t, x, s = w.curve(c)
+        check_topk(idx[c], S[c], o_idx[c], o_S[c], o_dense=S_or[c], abs_tol=1e-7 * s_bound(x, s),
+                   what=f"long-grid curve {c}")
+    mi, mo, ms_, Sd = run_multi(G, ctx, w, 12, [1, 3], 5)
+    for c in range(w.ncurves):
+        t, x, s = w.curve(c)
+        bound = s_bound(x, s)
+        for q, g in enumerate((1, 3)):
+            So = oracle.fpw_multi(t, x, s, w.freqs, 12, g)
+            Sg = So.max(axis=0)
+            o_i, o_s = oracle.topk(Sg, 9)
+            check_topk(mi[c, q], ms_[c, q], o_i, o_s, o_dense=Sg, abs_tol=1e-6 * bound, what=f"multi g={g} curve {c}")
+            for j in range(5):
+                if mi[c, q, j] >= 0:  # the reported offset is the best one at that frequency
+                    col = So[:, mi[c, q, j]]
+                    assert abs(col[mo[c, q, j]] - col.max()) <= 1e-4 * abs(col.max()) + 1e-6 * bound
+    ctx.close()
