@@ -134,7 +134,8 @@ struct TileShape {
 size_t tile_smem_bytes(int T, int R, int M, int NC, int k, int accum, int ngroups = 0);
 int tile_max_blocks_per_sm(int R, int phase_mode, int accum, int T, size_t smem, bool multi = false,
                            bool dump = false);
-bool tile_supported_R(int R);
+bool tile_supported_R(int R);                      // some tile kernel has R frequencies per thread
+bool tile_has_R(int R, int accum, bool multi);     // the kernel for this sum mode / several-M call has it
 // Launches the kernel for (R, phase, accum); several-M when a.ngroups > 0, the
 // bin-dumping instantiation when a.bins_out != NULL.
 cudaError_t launch_tile(const TileArgs& a, const TileShape& s, int phase_mode, int accum, int grid, cudaStream_t st);

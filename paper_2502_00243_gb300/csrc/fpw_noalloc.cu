@@ -171,6 +171,7 @@ extern "C" FPW_API int fpw_periodogram_batch_noalloc(void* stream, const fpw_par
   TileShape sh{};
   sh.threads = p.threads ? p.threads : 128;
   sh.R = p.freqs_per_thread ? p.freqs_per_thread : (wide ? 2 : (M <= 24 ? 4 : 2));
+  if (!tile_has_R(sh.R, p.accum, false)) return FPW_ENOTSUP;
   int NC = p.obs_chunk;
   if (!NC) {
     for (int blocks : {2, 1}) {

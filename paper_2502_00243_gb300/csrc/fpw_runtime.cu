@@ -186,11 +186,15 @@ bool valid_params(const fpw_params& p) {
 // sums); the observation chunk takes NC*(16 + 8|16) bytes. Precedence: explicit params > the context's tuned
 // table (fpw_ctx_set_shape) > the built-in defaults, which were measured on a
 // GB300 with ZTF-like curves (threads x frequencies-per-thread sweeps at
-// M = 10, 20, 50): R = 8 for M <= 12, R = 4 for M <= 24 (R = 2 when the
-// typical curve has fewer than 300 observations), R = 2 up to M = 64, R = 1
-// beyond, T = 128 (halved while the bins alone do not fit). NC: the largest
-// chunk that keeps two resident blocks per SM (one stages while the other
-// accumulates), else one block per SM.
+// M = 10, 16, 20, 24, 30, 40, 50): R = 8 for M <= 12, R = 6 for M <= 16, R = 4
+// for M <= 24, R = 3 for M <= 32 (R = 2 for these three when the typical curve
+// has fewer than 300 observations, as measured at M = 20; R = 6 and 3 for FP32
+// sums of one M only, else 4 and 2), R = 2 up to M = 64, R = 1 beyond, T = 128
+// (halved while the bins alone do not fit): about 80-96 bin pairs per thread
+// keep two blocks of four warps per SM and spread each observation's broadcast
+// over the most frequencies. NC: the largest chunk that keeps two resident
+// blocks per SM (one stages while the other accumulates), else one block per
+// SM.
 int choose_shape(fpw_ctx* ctx, const fpw_params& p, int M, int k, int64_t max_n, int64_t n_typ, int ngroups,
                  TileShape& out) {
   const bool wide = p.accum != FPW_ACCUM_FP32;  // 16-byte bins
@@ -199,8 +203,12 @@ int choose_shape(fpw_ctx* ctx, const fpw_params& p, int M, int k, int64_t max_n,
     R = 2;
   else if (M <= 12)
     R = 8;
+  else if (M <= 16 && ngroups == 0)
+    R = n_typ < 300 ? 2 : 6;
   else if (M <= 24)
     R = n_typ < 300 ? 2 : 4;
+  else if (M <= 32 && ngroups == 0)
+    R = n_typ < 300 ? 2 : 3;
   else if (M <= 32 || (M <= 50 && ngroups == 0))
     R = 2;
   else if (M <= 50) {  // several M: the per-frequency combination favours more warps
@@ -219,9 +227,13 @@ int choose_shape(fpw_ctx* ctx, const fpw_params& p, int M, int k, int64_t max_n,
       items = e.items ? e.items : 8;
     }
   if (ngroups > 0 && T > 256) T = 256;  // the several-M kernel's launch bound (table entries may be wider)
+  // R = 3 and 6 exist for FP32 sums of one M only: a table entry tuned there
+  // gives the neighbouring instantiated R to the other kernels
+  if (!tile_has_R(R, p.accum, ngroups > 0)) R = (R == 3) ? 2 : 4;
   if (p.threads) T = p.threads;
   if (p.items_per_slot) items = p.items_per_slot;
   if (p.freqs_per_thread) R = p.freqs_per_thread;
+  if (!tile_has_R(R, p.accum, ngroups > 0)) return FPW_ENOTSUP;
   if (p.obs_chunk) NC = p.obs_chunk;
   const bool fixedT = p.threads != 0;
   while (!fixedT && T > 32 && tile_smem_bytes(T, R, M, 32, k, p.accum, ngroups) > (size_t)ctx->smem_optin) T /= 2;

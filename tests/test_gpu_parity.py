@@ -94,6 +94,8 @@ RAGGED = [
     ([1500, 10, 800], 2500, 20, 5, {"peak_mode": 1}),
     ([600, 2100], 1999, 64, 7, {"inv_alpha2": 0.5}),
     ([50, 1700, 333], 2111, 55, 5, {}),
+    ([900, 2600, 31, 450], 3001, 30, 5, {"freqs_per_thread": 3}),
+    ([900, 2600, 31, 450], 2999, 16, 5, {"freqs_per_thread": 6, "threads": 96}),
 ]
 
 
@@ -167,7 +169,7 @@ def test_bins_fp32_phase_mismatch_within_analytic_margin(ctx, K):
 # frequency 0, the second the grid's end
 BIN_SHAPES = [(10, {}), (20, {}), (50, {}), (20, {"accum": 1}), (20, {"accum": 2}),
               (20, {"obs_chunk": 96}), (20, {"threads": 64, "freqs_per_thread": 8}),
-              (12, {"threads": 96, "freqs_per_thread": 1})]
+              (12, {"threads": 96, "freqs_per_thread": 1}), (16, {}), (30, {})]
 
 
 @pytest.mark.parametrize("case", range(len(BIN_SHAPES)))
@@ -184,6 +186,41 @@ def test_bins_every_tile_width_and_segment(ctx, case):
     T, R, NC, grid = ctx.last_shape()
     if "threads" in kw:
         assert (T, R) == (kw["threads"], kw["freqs_per_thread"])
+    if not kw:
+        assert R == {10: 8, 20: 4, 50: 2, 16: 6, 30: 3}[M]  # the default frequencies per thread
+
+
+def test_three_and_six_frequencies_per_thread_only_where_instantiated(ctx):
+    """R = 3 and 6 exist for FP32 sums of one M: asked for elsewhere they are
+    refused; a tuned table entry with them gives the other calls R = 2 or 4."""
+    w = L.ragged(81, [700, 1500, 40], 3000, M=30, k=4)
+    d = to_dev(w)
+    for kw in ({"freqs_per_thread": 3, "accum": 2}, {"freqs_per_thread": 6, "accum": 1}):
+        with pytest.raises(G.FPWError) as ei:
+            run_batch(ctx, w, d=d, params=P(**kw))
+        assert ei.value.code == G.FPW_ENOTSUP
+    C, k = w.ncurves, 4
+    mi = torch.empty(C * k, dtype=torch.int32, device="cuda")
+    mo, ms_ = torch.empty_like(mi), torch.empty(C * k, dtype=torch.float32, device="cuda")
+    with pytest.raises(G.FPWError) as ei:
+        G.fpw_periodogram_batch_multi(ctx, None, P(freqs_per_thread=3), d["offsets"], w.offsets, d["t"], d["x"],
+                                      d["sigma"], d["freqs"], 30, (3,), k, mi, mo, ms_)
+    assert ei.value.code == G.FPW_ENOTSUP
+    ref = run_batch(ctx, w, d=d, params=P(accum=2))
+    ctx.set_shape(1, 100, 0, 1 << 40, 128, 3, 0, 0)
+    try:
+        got = run_batch(ctx, w, d=d, params=P(accum=2))  # compensated sums: R = 2
+        assert ctx.last_shape()[1] == 2
+        np.testing.assert_array_equal(got[0], ref[0])
+        np.testing.assert_array_equal(got[1], ref[1])
+        G.fpw_periodogram_batch_multi(ctx, None, None, d["offsets"], w.offsets, d["t"], d["x"], d["sigma"],
+                                      d["freqs"], 30, (3,), k, mi, mo, ms_)
+        torch.cuda.synchronize()
+        assert ctx.last_shape()[1] == 2 and ctx.status() == 0
+        run_batch(ctx, w, d=d)  # FP32 sums of one M: the entry's R = 3
+        assert ctx.last_shape()[:2] == (128, 3)
+    finally:
+        ctx.clear_shapes()
 
 
 def test_bins_nonlinear_grid_direct_anchors(ctx):
@@ -265,7 +302,7 @@ def test_invalid_arguments_rejected_before_launch(ctx):
         G.fpw_periodogram_batch_ex(ctx, None, None, d["offsets"], bad_off, d["t"], d["x"], d["sigma"], d["freqs"], 4,
                                    2, idx, S)
     assert ei.value.code == G.FPW_EINVAL
-    for bad in (P(K=0), P(threads=48), P(freqs_per_thread=3), P(inv_alpha2=-1.0), P(phase_mode=9)):
+    for bad in (P(K=0), P(threads=48), P(freqs_per_thread=5), P(inv_alpha2=-1.0), P(phase_mode=9)):
         with pytest.raises(G.FPWError) as ei:
             G.fpw_periodogram_batch_ex(ctx, None, bad, d["offsets"], w.offsets, d["t"], d["x"], d["sigma"],
                                        d["freqs"], 4, 2, idx, S)
