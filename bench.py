@@ -44,7 +44,7 @@ SM_MAX_MHZ_NOMINAL = 2070.0
 SMEM_EVALS_PER_CLK_SM = 8  # 16 B (A, B) read-modify-write per evaluation at 128 B/clk/SM
 KERNELS_PER_STEP = 5  # prep, tile_dev, tile, merge, latch
 SWEEP_MS = (10, 20, 50)  # bin counts of the throughput sweep
-ENTROPY_INST_PER_EVAL = 10.9  # thread instructions per evaluation of the dense phase-entropy kernel (ncu, M = 20)
+ENTROPY_INST_PER_EVAL = 9.86  # thread instructions per evaluation of the dense phase-entropy kernel (ncu, M = 20)
 # DRAM bytes (read + write) of one tile-kernel launch at M = 20, from an ncu capture of a 1e4-curve sweep
 # batch over 2e4 frequencies (dram__bytes_read.sum + dram__bytes_write.sum). The kernel reads each curve
 # from DRAM once per launch (t and the staged weights, about 16.7 B per observation; per-tile re-reads

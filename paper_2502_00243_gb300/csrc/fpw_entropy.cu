@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(kEntThreads) entropy_dense_kernel(const double
                                                                     int64_t nfreq, int M, float* H_out) {
   extern __shared__ __align__(16) unsigned char smem[];
   ulonglong2* const sPD = reinterpret_cast<ulonglong2*>(smem);
-  unsigned* const cnt = reinterpret_cast<unsigned*>(sPD + kEntChunk);
+  unsigned* const cnt = reinterpret_cast<unsigned*>(sPD + kEntChunk + 1);  // one record of padding after the chunk
   __shared__ double s_tm[kEntThreads / 32];
   const int tid = threadIdx.x;
   const int64_t f0 = (int64_t)blockIdx.x * (kEntThreads * R);
@@ -76,20 +76,20 @@ __global__ void __launch_bounds__(kEntThreads) entropy_dense_kernel(const double
       sPD[i] = lin ? make_ulonglong2(phase_fixed64(ti, fa), phase_fixed64(ti, df))
                    : make_ulonglong2((unsigned long long)__double_as_longlong(ti), 0ull);
     }
+    if (tid == 0) sPD[c] = make_ulonglong2(0ull, 0ull);  // read by the last iteration's prefetch, never used
     __syncthreads();
     unsigned* const mine = cnt + tid;  // this thread's column of the [r][m][thread] counts
     if (lin) {
       ulonglong2 pd = sPD[0];
 #pragma unroll 2
       for (int i = 0; i < c; ++i) {
-        const ulonglong2 pdn = sPD[(i + 1 < c) ? i + 1 : i];
-        unsigned long long phi = pd.x + (unsigned long long)j0 * pd.y;
+        const ulonglong2 pdn = sPD[i + 1];  // i + 1 <= c <= kEntChunk: staged or the zeroed record
+        // the R phases are independent multiply-adds (no serial chain of 64-bit adds)
+        const unsigned long long phi0 = pd.x + (unsigned long long)j0 * pd.y;
         unsigned* sl[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-          sl[r] = mine + r * MT + bin_of_phase(phi, (unsigned)M) * kEntThreads;
-          phi += pd.y;
-        }
+        for (int r = 0; r < R; ++r)
+          sl[r] = mine + r * MT + bin_of_phase(phi0 + (unsigned long long)r * pd.y, (unsigned)M) * kEntThreads;
         unsigned v[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) v[r] = *sl[r];
@@ -189,7 +189,7 @@ cudaError_t launch_entropy_dense(const double* t, int64_t n, const double* freqs
   const void* fn = R == 4   ? reinterpret_cast<const void*>(&entropy_dense_kernel<4>)
                    : R == 2 ? reinterpret_cast<const void*>(&entropy_dense_kernel<2>)
                             : reinterpret_cast<const void*>(&entropy_dense_kernel<1>);
-  const size_t smem = (size_t)kEntChunk * 16 + (size_t)R * M * kEntThreads * 4;
+  const size_t smem = (size_t)(kEntChunk + 1) * 16 + (size_t)R * M * kEntThreads * 4;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int64_t per_block = (int64_t)kEntThreads * R;
