@@ -65,7 +65,9 @@ struct TileLayout {
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 // Shared-memory carve-up of one block: bins [R][M][T] of bin_bytes, the staged
-// {Phi, D} (16 B) and weights (bin_bytes) of NC observations, peak scratch.
+// {Phi, D} (16 B) and weights (bin_bytes) of NC observations plus two padding
+// records (read by the hot loop's prefetch past a chunk's last observation,
+// never used), peak scratch.
 __host__ __device__ inline TileLayout tile_layout(int T, int R, int M, int NC, size_t bin_bytes, int ngroups) {
   const size_t W = (size_t)T * R;
   const size_t tops = (size_t)(ngroups > 1 ? ngroups : 1) * FPW_MAX_TOPK;
@@ -74,9 +76,9 @@ __host__ __device__ inline TileLayout tile_layout(int T, int R, int M, int NC, s
   L.bins = o;
   o = align16(o + (size_t)R * M * T * bin_bytes);
   L.pd = o;
-  o = align16(o + (size_t)NC * 16);
+  o = align16(o + (size_t)(NC + 2) * 16);
   L.aw = o;
-  o = align16(o + (size_t)NC * bin_bytes);
+  o = align16(o + (size_t)(NC + 2) * bin_bytes);
   L.candS = o;
   o = align16(o + W * 8);
   L.candI = o;
@@ -282,6 +284,18 @@ __device__ __forceinline__ Block<P> make_block(unsigned char* smem, const TileAr
   return b;
 }
 
+// The two padding records after the staged chunk hold zeros (defined values
+// for the prefetch that reads them; made visible by the first item's barrier).
+template <class P>
+__device__ __forceinline__ void zero_padding(const Block<P>& b) {
+  if (b.tid < 2) {
+    b.sPD[b.NC + b.tid] = make_ulonglong2(0ull, 0ull);
+    typename P::In z;
+    bin_zero(z);
+    b.sAW[b.NC + b.tid] = z;
+  }
+}
+
 // Is the grid linear over the tile starting at s? The precomputed per-tile
 // deviation when available (tile starts sit at multiples of W-2, minus one),
 // else checked here (block-wide).
@@ -374,12 +388,11 @@ __device__ __forceinline__ void accumulate_tile(const TileArgs& args, const Bloc
           for (int r = 0; r < R; ++r) m[r] = bin_of_phase(f0 + (unsigned long long)r * p0.y, M);
         }
         In xv = sAW[0];
-        ulonglong2 pdn = sPD[cnt > 1 ? 1 : 0];
-        In xn = sAW[cnt > 1 ? 1 : 0];
+        ulonglong2 pdn = sPD[1];  // a padding record when cnt == 1
+        In xn = sAW[1];
         for (int i = 0; i < cnt; ++i) {
-          const int i2 = (i + 2 < cnt) ? i + 2 : cnt - 1;
-          const ulonglong2 pdnn = sPD[i2];
-          const In xnn = sAW[i2];
+          const ulonglong2 pdnn = sPD[i + 2];  // index <= cnt + 1 <= NC + 1: staged or padding
+          const In xnn = sAW[i + 2];
           Bin v[R];
 #pragma unroll
           for (int r = 0; r < R; ++r) v[r] = *reinterpret_cast<const Bin*>(my_bins + m[r] * T8 + (unsigned)r * MT8);
@@ -402,9 +415,8 @@ __device__ __forceinline__ void accumulate_tile(const TileArgs& args, const Bloc
         In xv = sAW[0];
 #pragma unroll 2
         for (int i = 0; i < cnt; ++i) {
-          const int in = (i + 1 < cnt) ? i + 1 : i;
-          const ulonglong2 pdn = sPD[in];
-          const In xn = sAW[in];
+          const ulonglong2 pdn = sPD[i + 1];  // index <= cnt <= NC: staged or padding
+          const In xn = sAW[i + 1];
           // the R phases are independent multiply-adds (no serial chain of 64-bit adds)
           const unsigned long long phi0 = pd.x + (unsigned long long)j0 * pd.y;
           unsigned m[R];
@@ -589,6 +601,7 @@ __global__ void __launch_bounds__(512) tile_kernel(const TileArgs args) {
     bin_zero(z);
     *reinterpret_cast<Bin*>(b.my_bins + (size_t)q * b.T8) = z;
   }
+  zero_padding(b);
 
   for (;;) {
     if (b.tid == 0) b.misc[0] = (int)atomicAdd(args.counter, 1u);
@@ -676,6 +689,7 @@ __global__ void __launch_bounds__(kMultiMaxThreads, 2) tile_kernel_multi(const T
   const A cal = (A)args.inv_alpha2;
 
   for (int q = 0; q < R * Mx; ++q) *reinterpret_cast<A2*>(b.my_bins + (size_t)q * b.T8) = make_float2(0.f, 0.f);
+  zero_padding(b);
 
   for (;;) {
     if (b.tid == 0) b.misc[0] = (int)atomicAdd(args.counter, 1u);
