@@ -49,7 +49,7 @@ def check(*bufs):
 
 
 SHAPES = [([0, 1, 31, 33, 700, 2500, 0, 64], 1021, 20, 5), ([5, 3000], 4097, 10, 64), ([900, 77], 3, 50, 7),
-          ([333, 1200, 1], 2050, 1, 3)]
+          ([333, 1200, 1], 2050, 1, 3), ([0, 1, 31, 700, 2500], 1021, 30, 5), ([5, 3000, 64], 777, 16, 7)]
 
 
 @pytest.mark.parametrize("case", range(len(SHAPES)))
