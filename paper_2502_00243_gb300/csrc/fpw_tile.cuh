@@ -152,18 +152,17 @@ __device__ __forceinline__ void bin_zero(float2& v) { v = make_float2(0.f, 0.f);
 __device__ __forceinline__ void bin_zero(double2& v) { v = make_double2(0.0, 0.0); }
 __device__ __forceinline__ void bin_zero(float4& v) { v = make_float4(0.f, 0.f, 0.f, 0.f); }
 
-// n / d for the reduce step: the fast reciprocal-based quotient (2 ulp) in the
-// normal range of d, correctly rounded division elsewhere; binary64 always
-// correctly rounded.
-__device__ __forceinline__ float quotient(float n, float d) {
-  return (d >= 1.17549435e-38f && d <= 8.5e37f) ? __fdividef(n, d) : n / d;
-}
-__device__ __forceinline__ double quotient(double n, double d) { return n / d; }
-
 // One bin's term A^2 / (B + 1/alpha^2) of Eq. 1; a bin whose denominator is 0 contributes 0.
+// FP32: the reciprocal-based quotient (2 ulp), branch-free (a branch to a
+// correctly rounded division for out-of-range denominators kept the compiler
+// from overlapping the terms of the reduce); a denominator outside
+// [2^-100, 2^100] is scaled by 2^-+64 into that range first, the numerator
+// alike, so the reciprocal stays accurate. Binary64: correctly rounded.
 __device__ __forceinline__ float bin_term(float2 v, float cal) {
   const float den = v.y + cal;
-  return (den > 0.f) ? quotient(v.x * v.x, den) : 0.f;
+  const float sc = den > 0x1p+100f ? 0x1p-64f : (den < 0x1p-100f ? 0x1p+64f : 1.0f);
+  const float q = __fdividef((v.x * v.x) * sc, den * sc);
+  return (den > 0.f) ? q : 0.f;
 }
 __device__ __forceinline__ double bin_term(double2 v, double cal) {
   const double den = v.y + cal;
@@ -585,8 +584,11 @@ __device__ __forceinline__ void item_end(const TileArgs& args, const Block<P>& b
   __syncthreads();
 }
 
+// (512, 1) sets the same 128-register ceiling as a bare 512-thread bound; with
+// it the compiler gives every instantiation the registers it needs, where the
+// bare bound led it to hold some to 64 registers and spill.
 template <int R, int PHASE, class P, bool DUMP>
-__global__ void __launch_bounds__(512) tile_kernel(const TileArgs args) {
+__global__ void __launch_bounds__(512, 1) tile_kernel(const TileArgs args) {
   using Bin = typename P::Bin;
   using A = typename P::S;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -634,11 +636,22 @@ __global__ void __launch_bounds__(512) tile_kernel(const TileArgs args) {
       for (int r = 0; r < R; ++r) {
         A acc = (A)0;
         unsigned char* col = b.my_bins + (size_t)r * b.MT8;
-        for (int m = 0; m < b.M; ++m) {
+        Bin z;
+        bin_zero(z);
+        int m = 0;
+        for (; m + 8 <= b.M; m += 8) {  // eight bins loaded before any is cleared: their loads overlap
+          Bin v[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) v[u] = *reinterpret_cast<const Bin*>(col + (size_t)(m + u) * b.T8);
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            *reinterpret_cast<Bin*>(col + (size_t)(m + u) * b.T8) = z;
+            acc += bin_term(v[u], cal);
+          }
+        }
+        for (; m < b.M; ++m) {
           Bin* p = reinterpret_cast<Bin*>(col + (size_t)m * b.T8);
           const Bin v = *p;
-          Bin z;
-          bin_zero(z);
           *p = z;
           acc += bin_term(v, cal);
         }
@@ -715,14 +728,28 @@ __global__ void __launch_bounds__(kMultiMaxThreads, 2) tile_kernel_multi(const T
       accumulate_tile<R, PHASE, P, false>(args, b, s, a, fa, lin, resident && staged_lin && lin, staged_lin, base,
                                           n, wi);
 
-      // inclusive prefix sums Q[m] of the M_max bins, in place, per r
+      // inclusive prefix sums Q[m] of the M_max bins, in place, per r; eight
+      // bins are loaded before any of them is stored back, so the loads of a
+      // chunk are in flight together (the bins of one thread form a dependent
+      // chain otherwise: a load cannot pass the previous bin's store)
       float2 total[R];
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         A2* col = reinterpret_cast<A2*>(b.my_bins + (size_t)r * b.MT8);
         const int st = b.T;  // stride between bins, in A2 units
         A2 run = make_float2(0.f, 0.f);
-        for (int m = 0; m < Mx; ++m) {
+        int m = 0;
+        for (; m + 8 <= Mx; m += 8) {
+          A2 v[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) v[u] = col[(m + u) * st];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            run = bin_add(run, v[u]);
+            col[(m + u) * st] = run;
+          }
+        }
+        for (; m < Mx; ++m) {
           run = bin_add(run, col[m * st]);
           col[m * st] = run;
         }
@@ -743,19 +770,21 @@ __global__ void __launch_bounds__(kMultiMaxThreads, 2) tile_kernel_multi(const T
             // window j spans bins [j gs + o, j gs + o + gs - 1]: its sum is
             // Q[end] - Q[start - 1], and its end is the next window's start - 1,
             // so one prefix value is read per window (carried in `prev`)
-            A2 prev = (o > 0) ? col[(o - 1) * st] : make_float2(0.f, 0.f);
-            for (int j = 0; j < Mg; ++j) {
-              const int p1 = j * gs + o + gs - 1;
-              A2 w;
-              if (p1 < Mx) {
-                const A2 q = col[p1 * st];
-                w = f2sub(q, prev);
-                prev = q;
-              } else {  // the last window wraps past bin M_max - 1 (then o >= 1)
-                w = bin_add(f2sub(total[r], prev), col[(p1 - Mx) * st]);
-              }
-              acc += bin_term(w, cal);
+            const A2 q0 = (o > 0) ? col[(o - 1) * st] : make_float2(0.f, 0.f);
+            A2 prev = q0;
+            // the windows that end below bin M_max: independent loads (no
+            // stores here), unrolled so that they issue together; the terms
+            // are added in window order
+            const int nin = (o > 0) ? Mg - 1 : Mg;
+            const A2* e = col + (size_t)(o + gs - 1) * st;
+#pragma unroll 4
+            for (int j = 0; j < nin; ++j) {
+              const A2 q = e[(size_t)j * gs * st];
+              acc += bin_term(f2sub(q, prev), cal);
+              prev = q;
             }
+            // o >= 1: the last window wraps past bin M_max - 1 and ends at o - 1
+            if (o > 0) acc += bin_term(bin_add(f2sub(total[r], prev), q0), cal);
             if (acc > best) {
               best = acc;
               bo = o;
