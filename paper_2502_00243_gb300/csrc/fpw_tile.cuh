@@ -39,7 +39,8 @@
 // compensation terms (A, B, cA, cB), where each addition is an exact two-sum
 // whose rounding error, plus the low part of the staged term, goes to the
 // compensation term (the weights are staged as hi + lo FP32 pairs), so the
-// sums carry about 48 significant bits.
+// sums carry about 48 significant bits; each bin's term is then taken from
+// hi + lo rounded once to FP32, and S is accumulated in binary64.
 //
 // DUMP instantiations additionally write the bin m of every (observation,
 // owned frequency k) with bins_k0 <= k < bins_k1 to args.bins_out, from the
@@ -168,9 +169,12 @@ __device__ __forceinline__ double bin_term(double2 v, double cal) {
   const double den = v.y + cal;
   return (den > 0.0) ? v.x * v.x / den : 0.0;
 }
+// Compensated: the sums' value hi + lo rounded once to FP32 (the compensation
+// already holds their rounding error), the term as in the FP32 policy (about
+// 3e-7 relative), S accumulated in binary64. A binary64 division per bin took
+// 28 % of the kernel's time at M = 20 and 44 % at M = 50.
 __device__ __forceinline__ double bin_term(float4 v, double cal) {
-  const double A = (double)v.x + (double)v.z, den = ((double)v.y + (double)v.w) + cal;
-  return (den > 0.0) ? A * A / den : 0.0;
+  return (double)bin_term(make_float2(v.x + v.z, v.y + v.w), (float)cal);
 }
 
 __device__ __forceinline__ float2 f2sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
