@@ -209,7 +209,7 @@ int choose_shape(fpw_ctx* ctx, const fpw_params& p, int M, int k, int64_t max_n,
     R = n_typ < 300 ? 2 : 4;
   else if (M <= 32 && ngroups == 0)
     R = n_typ < 300 ? 2 : 3;
-  else if (M <= 32 || (M <= 50 && ngroups == 0))
+  else if (M <= 40 || (M <= 50 && ngroups == 0))  // several M at M_max = 40: 1.23e12 against 1.17e12 at T = 256, R = 1
     R = 2;
   else if (M <= 50) {  // several M: the per-frequency combination favours more warps
     T = 256;
