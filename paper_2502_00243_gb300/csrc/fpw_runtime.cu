@@ -292,6 +292,14 @@ Plan* build_plan(fpw_ctx* ctx, const int64_t* off, int64_t C, int64_t F, const T
   for (int64_t c = 0; c < C; ++c) {
     const double cc = (double)(off[c + 1] - off[c] + 32) * (double)F;
     int64_t nseg = (int64_t)std::llround(cc / target);
+    // A curve that would be cut finer than three tiles per item (a single long
+    // curve, cut for load balance) gets whole rounds of the resident blocks,
+    // each item at least three tiles: an item's prologue, restaging and
+    // candidate row cost about a tile's latency, and equal items that do not
+    // fill whole rounds leave blocks idle. 1000 observations x 1e6
+    // frequencies: 0.635 -> 0.60 ms of tile kernel, 0.76 -> 0.67 ms per call.
+    const int64_t rounds = tiles / (3 * (int64_t)resident);
+    if (nseg > tiles / 3 && rounds >= 1) nseg = rounds * resident;
     nseg = std::max<int64_t>(1, std::min<int64_t>(nseg, tiles));
     base[c + 1] = base[c] + (int32_t)nseg;
     for (int64_t q = 0; q < nseg; ++q) {
