@@ -7,6 +7,7 @@
 // plain form (one launch per curve), and the host-buffer end-to-end entry.
 #include <algorithm>
 #include <cmath>
+#include <utility>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -285,13 +286,13 @@ Plan* build_plan(fpw_ctx* ctx, const int64_t* off, int64_t C, int64_t F, const T
   double total = 0.0;
   for (int64_t c = 0; c < C; ++c) total += (double)(off[c + 1] - off[c] + 32) * (double)F;
   const double target = std::max(total / ((double)sh.items * resident), 32.0 * (double)Wown * 16.0);
-  std::vector<WorkItem> items;
-  std::vector<double> cost;
-  std::vector<int32_t> base((size_t)C + 1, 0);
-  items.reserve((size_t)C);
+  std::vector<double> ccv((size_t)C);
+  std::vector<int64_t> nseg((size_t)C);
+  bool all_split = C > 1;
   for (int64_t c = 0; c < C; ++c) {
     const double cc = (double)(off[c + 1] - off[c] + 32) * (double)F;
-    int64_t nseg = (int64_t)std::llround(cc / target);
+    ccv[(size_t)c] = cc;
+    int64_t n = (int64_t)std::llround(cc / target);
     // A curve that would be cut finer than three tiles per item (a single long
     // curve, cut for load balance) gets whole rounds of the resident blocks,
     // each item at least three tiles: an item's prologue, restaging and
@@ -299,11 +300,43 @@ Plan* build_plan(fpw_ctx* ctx, const int64_t* off, int64_t C, int64_t F, const T
     // fill whole rounds leave blocks idle. 1000 observations x 1e6
     // frequencies: 0.635 -> 0.60 ms of tile kernel, 0.76 -> 0.67 ms per call.
     const int64_t rounds = tiles / (3 * (int64_t)resident);
-    if (nseg > tiles / 3 && rounds >= 1) nseg = rounds * resident;
-    nseg = std::max<int64_t>(1, std::min<int64_t>(nseg, tiles));
-    base[c + 1] = base[c] + (int32_t)nseg;
-    for (int64_t q = 0; q < nseg; ++q) {
-      const int64_t t0 = tiles * q / nseg, t1 = tiles * (q + 1) / nseg;
+    if (n > tiles / 3 && rounds >= 1) n = rounds * resident;
+    n = std::max<int64_t>(1, std::min<int64_t>(n, tiles));
+    nseg[(size_t)c] = n;
+    if (n < 2) all_split = false;
+  }
+  // Every curve cut (a few long curves): the item count is made whole rounds
+  // of the resident blocks, shared by cost with the largest remainders (20
+  // equal curves over 2e6 frequencies and 152 blocks: 1220 items, a ninth
+  // round nearly empty, became 1216).
+  int64_t nall = 0;
+  for (int64_t c = 0; c < C; ++c) nall += nseg[(size_t)c];
+  if (all_split && nall % resident != 0) {
+    const int64_t want = std::max<int64_t>(resident, (nall + resident / 2) / resident * resident);
+    std::vector<std::pair<double, int64_t>> frac;
+    int64_t got = 0;
+    for (int64_t c = 0; c < C; ++c) {
+      const double share = (double)want * ccv[(size_t)c] / total;
+      const int64_t f = std::max<int64_t>(1, std::min<int64_t>((int64_t)std::floor(share), tiles));
+      nseg[(size_t)c] = f;
+      got += f;
+      if (f < tiles) frac.emplace_back(share - std::floor(share), c);
+    }
+    std::stable_sort(frac.begin(), frac.end(), [](const std::pair<double, int64_t>& x, const std::pair<double, int64_t>& y) {
+      return x.first > y.first;
+    });
+    for (size_t i = 0; i < frac.size() && got < want; ++i, ++got) nseg[(size_t)frac[i].second] += 1;
+  }
+  std::vector<WorkItem> items;
+  std::vector<double> cost;
+  std::vector<int32_t> base((size_t)C + 1, 0);
+  items.reserve((size_t)C);
+  for (int64_t c = 0; c < C; ++c) {
+    const double cc = ccv[(size_t)c];
+    const int64_t ns = nseg[(size_t)c];
+    base[c + 1] = base[c] + (int32_t)ns;
+    for (int64_t q = 0; q < ns; ++q) {
+      const int64_t t0 = tiles * q / ns, t1 = tiles * (q + 1) / ns;
       WorkItem w;
       w.curve = (int32_t)c;
       w.f_lo = (int32_t)(t0 * Wown);
