@@ -185,48 +185,56 @@ __device__ __forceinline__ double warp_max(double v) {
   return v;
 }
 
+// Order-preserving map of a double to an unsigned integer (larger value, larger
+// image), and its inverse.
+__device__ __forceinline__ unsigned long long rank_bits(double s) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(s);
+  return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double from_rank_bits(unsigned long long r) {
+  return __longlong_as_double((long long)((r >> 63) ? (r & 0x7fffffffffffffffull) : ~r));
+}
+
 // Selects the best kk entries of (top list) + (candidate list) into the top
 // list, ranked by S descending then key ascending. Executed by one warp.
 // Entries with key < 0 are empty. kk <= FPW_MAX_TOPK (two results per lane).
+// Round q takes the best entry ranked after round q-1's pick (keys are unique
+// within an item, so no entry needs marking): each lane's best over its
+// strided share, then the warp's from three redux.sync maxima over (S's
+// order-preserving high word, its low word, the inverted key).
 __device__ void warp_merge_topk(double* topS, int* topI, int kk, double* cS, int* cI, int cnt, int lane) {
   double keepS[2] = {-INFINITY, -INFINITY};
   int keepI[2] = {-1, -1};
   const int pool = kk + cnt;
+  unsigned long long prev_r = 0ull;
+  unsigned prev_k = 0u;
   for (int q = 0; q < kk; ++q) {
-    double bs = -INFINITY;
-    int bi = -1, bp = -1;
+    unsigned long long br = 0ull;  // 0: nothing (no double maps to 0 here)
+    unsigned bk = 0u;
     for (int e = lane; e < pool; e += 32) {
-      const double s = (e < kk) ? topS[e] : cS[e - kk];
       const int i = (e < kk) ? topI[e] : cI[e - kk];
-      if (i >= 0 && (bp < 0 || ranks_before(s, i, bs, bi))) {
-        bs = s;
-        bi = i;
-        bp = e;
+      if (i < 0) continue;
+      const unsigned long long r = rank_bits((e < kk) ? topS[e] : cS[e - kk]);
+      const unsigned kx = ~(unsigned)i;
+      const bool after = (q == 0) || r < prev_r || (r == prev_r && kx < prev_k);
+      if (after && (r > br || (r == br && kx > bk))) {
+        br = r;
+        bk = kx;
       }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const double os = __shfl_xor_sync(0xffffffffu, bs, o);
-      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      const int op = __shfl_xor_sync(0xffffffffu, bp, o);
-      if (op >= 0 && (bp < 0 || ranks_before(os, oi, bs, bi))) {
-        bs = os;
-        bi = oi;
-        bp = op;
-      }
-    }
-    if (lane == 0 && bp >= 0) {
-      if (bp < kk)
-        topI[bp] = -1;
-      else
-        cI[bp - kk] = -1;
-    }
+    const unsigned hi = __reduce_max_sync(0xffffffffu, (unsigned)(br >> 32));
+    const unsigned lo = __reduce_max_sync(0xffffffffu, (unsigned)(br >> 32) == hi ? (unsigned)br : 0u);
+    const unsigned long long wr = ((unsigned long long)hi << 32) | lo;
+    const unsigned wk = __reduce_max_sync(0xffffffffu, br == wr ? bk : 0u);
+    if (wr == 0ull) break;  // every entry taken
+    prev_r = wr;
+    prev_k = wk;
     if (lane == (q & 31)) {
-      keepS[q >> 5] = (bp >= 0) ? bs : -INFINITY;
-      keepI[q >> 5] = (bp >= 0) ? bi : -1;
+      keepS[q >> 5] = from_rank_bits(wr);
+      keepI[q >> 5] = (int)~wk;
     }
-    __syncwarp();
   }
+  __syncwarp();
   for (int q = lane; q < kk; q += 32) {
     topS[q] = keepS[q >> 5];
     topI[q] = keepI[q >> 5];
