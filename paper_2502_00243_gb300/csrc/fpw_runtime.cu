@@ -311,7 +311,7 @@ Plan* build_plan(fpw_ctx* ctx, const int64_t* off, int64_t C, int64_t F, const T
   // round nearly empty, became 1216).
   int64_t nall = 0;
   for (int64_t c = 0; c < C; ++c) nall += nseg[(size_t)c];
-  if (all_split && nall % resident != 0) {
+  if (all_split && nall >= resident && nall % resident != 0) {  // fewer items: the minimum item size binds
     const int64_t want = std::max<int64_t>(resident, (nall + resident / 2) / resident * resident);
     std::vector<std::pair<double, int64_t>> frac;
     int64_t got = 0;
