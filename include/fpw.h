@@ -85,7 +85,7 @@ typedef struct fpw_params {
   int K;                /* FPW_PHASE_FP32 only: re-anchor interval in frequencies (default 256) */
   int peak_mode;        /* FPW_PEAK_* (default FPW_PEAK_LOCALMAX) */
   int threads;          /* 0 = tuned; else threads per block (multiple of 32, 32..512) */
-  int freqs_per_thread; /* 0 = tuned; else 1, 2, 4 or 8, or 3 or 6 with FPW_ACCUM_FP32 on a call of one M
+  int freqs_per_thread; /* 0 = tuned; else 1, 2, 4 or 8, or 3, 5 or 6 with FPW_ACCUM_FP32 on a call of one M
                            (FPW_ENOTSUP on the other calls) */
   int obs_chunk;        /* 0 = tuned; else observations staged in shared memory per pass (>= 32) */
   int use_graph;        /* 1 = capture the launch sequence in a CUDA graph and replay it on identical calls */
@@ -302,12 +302,12 @@ FPW_API int fpw_periodogram_batch_noalloc(void* stream, const fpw_params* params
                                           int M, int k, int32_t* topk_idx, float* topk_S);
 
 /* Tuned kernel shapes. Adds a shape -- threads per block (multiple of 32,
- * 32..512), frequencies per thread (1, 2, 3, 4, 6 or 8), observations per
+ * 32..512), frequencies per thread (1, 2, 3, 4, 5, 6 or 8), observations per
  * pass (0 = largest that keeps two blocks per SM) and work items per resident
  * block (0 = 8; see fpw_params.items_per_slot) -- used for batched and single
  * calls whose bin count lies in [M_lo, M_hi] and whose observation-weighted
  * mean curve size lies in [n_lo, n_hi). Later entries take precedence; explicit
- * fpw_params fields override the table. An entry's 3 or 6 frequencies per
+ * fpw_params fields override the table. An entry's 3, 5 or 6 frequencies per
  * thread apply to calls of one M with FP32 sums; the other calls in its range
  * take 2 or 4 instead. The autotuner
  * (paper_2502_00243_gb300/autotune.py) measures candidates and fills it.

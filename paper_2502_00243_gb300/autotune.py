@@ -23,9 +23,9 @@ import numpy as np
 
 from . import Context, FPWError, fpw_params_default, fpw_periodogram_batch_ex
 
-CANDIDATES = ((128, 8), (128, 6), (128, 4), (128, 3), (128, 2), (128, 1), (256, 4), (256, 2), (256, 1), (64, 8),
-              (64, 4), (192, 2))
-SCHEDULES = ((0, 8), (0, 4), (0, 16), (256, 8), (512, 8))  # (observations per pass, items per resident block)
+CANDIDATES = ((128, 8), (128, 6), (128, 5), (128, 4), (128, 3), (128, 2), (128, 1), (256, 4), (256, 2), (256, 1),
+              (64, 8), (64, 4), (192, 2))
+SCHEDULES = ((0, 8), (0, 4), (0, 16), (128, 8), (256, 8), (512, 8))  # (observations per pass, items per resident block)
 DEFAULT_MS = (10, 20, 50)
 DEFAULT_BUCKETS = ((0, 300), (300, 1000), (1000, 1 << 40))
 

@@ -187,15 +187,15 @@ bool valid_params(const fpw_params& p) {
 // sums); the observation chunk takes NC*(16 + 8|16) bytes. Precedence: explicit params > the context's tuned
 // table (fpw_ctx_set_shape) > the built-in defaults, which were measured on a
 // GB300 with ZTF-like curves (threads x frequencies-per-thread sweeps at
-// M = 10, 16, 20, 24, 30, 40, 50): R = 8 for M <= 12, R = 6 for M <= 16, R = 4
-// for M <= 24, R = 3 for M <= 32 (R = 2 for these three when the typical curve
-// has fewer than 300 observations, as measured at M = 20; R = 6 and 3 for FP32
-// sums of one M only, else 4 and 2), R = 2 up to M = 64, R = 1 beyond, T = 128
-// (halved while the bins alone do not fit): about 80-96 bin pairs per thread
-// keep two blocks of four warps per SM and spread each observation's broadcast
-// over the most frequencies. NC: the largest chunk that keeps two resident
-// blocks per SM (one stages while the other accumulates), else one block per
-// SM.
+// M = 10, 16, 20, 24, 30, 40, 50): R = 8 for M <= 12, R = 6 for M <= 16, R = 5
+// for M <= 20, R = 4 for M <= 25, R = 3 for M <= 33 (R = 2 for these when the
+// typical curve has fewer than 300 observations, as measured at M = 20; R = 6, 5
+// and 3 for FP32 sums of one M only, else 4 and 2), R = 2 up to M = 64, R = 1
+// beyond, T = 128 (halved while the bins alone do not fit): up to about 100 bin
+// pairs per thread keep two blocks of four warps per SM and spread each
+// observation's broadcast over the most frequencies. NC: the largest chunk that
+// keeps two resident blocks per SM (one stages while the other accumulates) if
+// that is at least 128 observations, else one block per SM.
 int choose_shape(fpw_ctx* ctx, const fpw_params& p, int M, int k, int64_t max_n, int64_t n_typ, int ngroups,
                  TileShape& out) {
   const bool wide = p.accum != FPW_ACCUM_FP32;  // 16-byte bins
@@ -206,9 +206,11 @@ int choose_shape(fpw_ctx* ctx, const fpw_params& p, int M, int k, int64_t max_n,
     R = 8;
   else if (M <= 16 && ngroups == 0)
     R = n_typ < 300 ? 2 : 6;
-  else if (M <= 24)
+  else if (M <= 20 && ngroups == 0)
+    R = n_typ < 300 ? 2 : 5;
+  else if (M <= 24 || (M <= 25 && ngroups == 0))
     R = n_typ < 300 ? 2 : 4;
-  else if (M <= 32 && ngroups == 0)
+  else if (M <= 33 && ngroups == 0)
     R = n_typ < 300 ? 2 : 3;
   else if (M <= 40 || (M <= 50 && ngroups == 0))  // several M at M_max = 40: 1.23e12 against 1.17e12 at T = 256, R = 1
     R = 2;
@@ -257,7 +259,10 @@ int choose_shape(fpw_ctx* ctx, const fpw_params& p, int M, int k, int64_t max_n,
         else
           hi = mid - 32;
       }
-      if (blocks == 2 && lo < 256 && lo < want_nc) continue;  // too small a chunk: one block per SM instead
+      // too small a chunk: one block per SM instead (two blocks with 128-160
+      // observations per pass ran M = 20, R = 5 at 2.0e12 evals/s, one block
+      // with a larger chunk 1.5e12)
+      if (blocks == 2 && lo < 128 && lo < want_nc) continue;
       NC = lo;
       break;
     }

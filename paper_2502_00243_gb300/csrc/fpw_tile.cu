@@ -39,7 +39,8 @@ __global__ void tile_dev_kernel(const double* freqs, int64_t F, int W, int64_t t
 const void* pick(int R, int phase_mode, int accum, bool multi, bool dump) {
   if (multi) return dump ? nullptr : tile_fn_multi(R, phase_mode);
   switch (accum) {
-    case FPW_ACCUM_FP32: return (R == 3 || R == 6) ? tile_fn_f32_odd(R, phase_mode, dump) : tile_fn_f32(R, phase_mode, dump);
+    case FPW_ACCUM_FP32:
+      return (R == 3 || R == 5 || R == 6) ? tile_fn_f32_odd(R, phase_mode, dump) : tile_fn_f32(R, phase_mode, dump);
     case FPW_ACCUM_FP64: return tile_fn_f64(R, phase_mode, dump);
     case FPW_ACCUM_FP32_COMP: return tile_fn_comp(R, phase_mode, dump);
     default: return nullptr;
@@ -52,15 +53,15 @@ size_t tile_smem_bytes(int T, int R, int M, int NC, int /*k*/, int accum, int ng
   return tile_layout(T, R, M, NC, accum_bin_bytes(accum), ngroups).total;
 }
 
-bool tile_supported_R(int R) { return R == 1 || R == 2 || R == 3 || R == 4 || R == 6 || R == 8; }
+bool tile_supported_R(int R) { return R >= 1 && R <= 8 && R != 7; }
 
 bool tile_has_R(int R, int accum, bool multi) {
   if (R == 1 || R == 2 || R == 4 || R == 8) return true;
-  return (R == 3 || R == 6) && accum == FPW_ACCUM_FP32 && !multi;
+  return (R == 3 || R == 5 || R == 6) && accum == FPW_ACCUM_FP32 && !multi;
 }
 
 cudaError_t tile_init_attributes(int max_smem) {
-  for (int R : {3, 6})
+  for (int R : {3, 5, 6})
     for (int ph : {FPW_PHASE_FIXED64, FPW_PHASE_FP32})
       for (bool dump : {false, true}) {
         cudaError_t e =

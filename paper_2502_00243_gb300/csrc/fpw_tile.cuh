@@ -54,7 +54,7 @@ namespace fpw {
 
 // Per-translation-unit kernel getters (fpw_tile_*.cu).
 const void* tile_fn_f32(int R, int phase_mode, bool dump);
-const void* tile_fn_f32_odd(int R, int phase_mode, bool dump);  // R = 3, 6
+const void* tile_fn_f32_odd(int R, int phase_mode, bool dump);  // R = 3, 5, 6
 const void* tile_fn_f64(int R, int phase_mode, bool dump);
 const void* tile_fn_comp(int R, int phase_mode, bool dump);
 const void* tile_fn_multi(int R, int phase_mode);

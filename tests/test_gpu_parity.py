@@ -96,6 +96,7 @@ RAGGED = [
     ([50, 1700, 333], 2111, 55, 5, {}),
     ([900, 2600, 31, 450], 3001, 30, 5, {"freqs_per_thread": 3}),
     ([900, 2600, 31, 450], 2999, 16, 5, {"freqs_per_thread": 6, "threads": 96}),
+    ([900, 2600, 31, 450], 3001, 19, 5, {"freqs_per_thread": 5, "threads": 128, "obs_chunk": 128}),
 ]
 
 
@@ -187,15 +188,16 @@ def test_bins_every_tile_width_and_segment(ctx, case):
     if "threads" in kw:
         assert (T, R) == (kw["threads"], kw["freqs_per_thread"])
     if not kw:
-        assert R == {10: 8, 20: 4, 50: 2, 16: 6, 30: 3}[M]  # the default frequencies per thread
+        assert R == {10: 8, 20: 5, 50: 2, 16: 6, 30: 3}[M]  # the default frequencies per thread
 
 
-def test_three_and_six_frequencies_per_thread_only_where_instantiated(ctx):
-    """R = 3 and 6 exist for FP32 sums of one M: asked for elsewhere they are
+def test_three_five_and_six_frequencies_per_thread_only_where_instantiated(ctx):
+    """R = 3, 5 and 6 exist for FP32 sums of one M: asked for elsewhere they are
     refused; a tuned table entry with them gives the other calls R = 2 or 4."""
     w = L.ragged(81, [700, 1500, 40], 3000, M=30, k=4)
     d = to_dev(w)
-    for kw in ({"freqs_per_thread": 3, "accum": 2}, {"freqs_per_thread": 6, "accum": 1}):
+    for kw in ({"freqs_per_thread": 3, "accum": 2}, {"freqs_per_thread": 5, "accum": 2},
+               {"freqs_per_thread": 6, "accum": 1}):
         with pytest.raises(G.FPWError) as ei:
             run_batch(ctx, w, d=d, params=P(**kw))
         assert ei.value.code == G.FPW_ENOTSUP
@@ -302,7 +304,7 @@ def test_invalid_arguments_rejected_before_launch(ctx):
         G.fpw_periodogram_batch_ex(ctx, None, None, d["offsets"], bad_off, d["t"], d["x"], d["sigma"], d["freqs"], 4,
                                    2, idx, S)
     assert ei.value.code == G.FPW_EINVAL
-    for bad in (P(K=0), P(threads=48), P(freqs_per_thread=5), P(inv_alpha2=-1.0), P(phase_mode=9)):
+    for bad in (P(K=0), P(threads=48), P(freqs_per_thread=7), P(inv_alpha2=-1.0), P(phase_mode=9)):
         with pytest.raises(G.FPWError) as ei:
             G.fpw_periodogram_batch_ex(ctx, None, bad, d["offsets"], w.offsets, d["t"], d["x"], d["sigma"],
                                        d["freqs"], 4, 2, idx, S)
