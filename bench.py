@@ -363,7 +363,11 @@ def run_gb300(args):
     if not args.no_autotune:  # a few seconds: shapes and schedules for the bin counts timed below
         from paper_2502_00243_gb300 import autotune
         t_tune = time.perf_counter()
-        tuned = {"entries": autotune.tune(ctx, Ms=(args.M, *other_Ms))}
+        h0 = host[batch_of[0]]  # a size-stratified sample of the workload's own curves
+        tuned = {"entries": autotune.tune_batch(ctx, h0[0], h0[1], h0[2], h0[3], float(F_grid[0]),
+                                                float(F_grid[-1]), (args.M, *other_Ms), k=k),
+                 "on": f"a size-stratified sample of batch {batch_of[0]}'s curves over 2e4 linear frequencies "
+                       f"spanning the grid"}
         tuned["seconds"] = round(time.perf_counter() - t_tune, 1)
     params = G.fpw_params_default()
     stream = torch.cuda.current_stream()

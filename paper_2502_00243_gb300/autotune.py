@@ -6,8 +6,10 @@ events around the tile kernel on its stream) and installs the fastest in a
 context's shape table (``fpw_ctx_set_shape``), in two stages: threads per block
 x frequencies per thread, then, for the best of those, the observations staged
 per pass (which set the blocks per SM) x the work items per resident block
-(the segment size of the persistent schedule's curve-to-block mapping). The
-table can be saved to / loaded from JSON.
+(the segment size of the persistent schedule's curve-to-block mapping).
+``tune`` measures synthetic curves of one size per bucket; ``tune_batch``
+measures a size-stratified sample of a workload's own curves. The table can
+be saved to / loaded from JSON.
 
 Shapes matter because the kernel is bound by the shared-memory pipe: every
 (thread, frequency) slot holds M (A, B) bin pairs, so M and the frequencies
@@ -120,6 +122,76 @@ def tune(ctx: Context, Ms=DEFAULT_MS, buckets=DEFAULT_BUCKETS, *, nfreq=50_000, 
                  "freqs_per_thread": best[1], "obs_chunk": sched[0], "items_per_slot": sched[1],
                  "geval_s": sched[2] / 1e9, "M": M, "n": n}
             entries.append(e)
+    if apply:
+        install(ctx, entries)
+    return entries
+
+
+def n_typical(offsets_h) -> int:
+    """The observation-weighted mean curve size sum(n^2) / sum(n) of a batch:
+    the curve-size key under which the library looks a batch up in the shape
+    table."""
+    n = np.diff(np.asarray(offsets_h, dtype=np.int64)).astype(np.float64)
+    s = float(n.sum())
+    return int(float((n * n).sum()) / s) if s > 0 else 0
+
+
+def stratified_sample(offsets_h, t, x, sigma, ncurves):
+    """Up to ``ncurves`` curves of a host batch taken evenly through its curves
+    sorted by size (so the sample keeps the batch's size mix), as a new host
+    batch (offsets, t, x, sigma)."""
+    off = np.asarray(offsets_h, dtype=np.int64)
+    C = off.shape[0] - 1
+    order = np.argsort(np.diff(off), kind="stable")
+    pick = order[np.linspace(0, C - 1, min(ncurves, C)).round().astype(np.int64)] if C > 0 else order
+    pick = np.unique(pick)
+    sizes = off[pick + 1] - off[pick]
+    sub_off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    rows = np.concatenate([np.arange(off[c], off[c + 1]) for c in pick]) if pick.size else np.zeros(0, np.int64)
+    return sub_off, np.asarray(t)[rows], np.asarray(x)[rows], np.asarray(sigma)[rows]
+
+
+def tune_batch(ctx: Context, offsets_h, t, x, sigma, f_lo: float, f_hi: float, Ms, *, k=5, sample_curves=4000,
+               nfreq=20_000, candidates=CANDIDATES, schedules=SCHEDULES, apply=True, log=None):
+    """Tune the shape on a workload's own curves rather than on curves of one
+    size: a batch whose sizes are spread (e.g. 100 to 3000 observations) can
+    favour another shape than uniform curves of its typical size. Times every
+    candidate (then every schedule for the best) on a size-stratified sample
+    of the host batch over ``nfreq`` linear frequencies in [f_lo, f_hi], for
+    each bin count in ``Ms``, and installs one entry per M covering curve sizes
+    within a factor of two of the batch's typical size (later entries take
+    precedence, so these override a generic table for such batches)."""
+    import torch
+    nt = n_typical(offsets_h)
+    off, ts, xs, ss = stratified_sample(offsets_h, t, x, sigma, sample_curves)
+    dev = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (off, ts, xs, ss)]
+    freqs = torch.linspace(float(f_lo), float(f_hi), nfreq, dtype=torch.float64, device="cuda")
+    evals = float(off[-1]) * nfreq
+    entries = []
+    for M in sorted(set(int(m) for m in Ms)):
+        best = None
+        for T, R in candidates:
+            ms = measure(ctx, dev, off, freqs, M, k, T, R)
+            if ms is None:
+                continue
+            rate = evals / (ms / 1e3)
+            if log:
+                log(f"batch M={M} T={T} R={R}: {rate / 1e9:.1f} Geval/s")
+            if best is None or rate > best[2]:
+                best = (T, R, rate)
+        if best is None:
+            continue
+        sched = (0, 0, best[2])
+        for NC, items in schedules:
+            ms = measure(ctx, dev, off, freqs, M, k, best[0], best[1], NC=NC, items=items)
+            if ms is None:
+                continue
+            rate = evals / (ms / 1e3)
+            if rate > sched[2]:
+                sched = (NC, items, rate)
+        entries.append({"M_lo": M, "M_hi": M, "n_lo": nt // 2, "n_hi": 2 * nt + 1, "threads": best[0],
+                        "freqs_per_thread": best[1], "obs_chunk": sched[0], "items_per_slot": sched[1],
+                        "geval_s": sched[2] / 1e9, "M": M, "n": nt, "sample_curves": int(off.shape[0] - 1)})
     if apply:
         install(ctx, entries)
     return entries

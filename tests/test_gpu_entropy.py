@@ -97,3 +97,30 @@ def test_entropy_at_batch_peaks(G):
     torch.cuda.synchronize()
     assert torch.isnan(H_[:2]).all() and torch.isnan(z_[:2]).all()
     ctx.close()
+
+
+@pytest.mark.parametrize("N", [65535, 65536])
+def test_dense_phase_entropy_large_counts(G, N):
+    """Counts as large as N around 2^16, from a grid whose first frequency is 0
+    (every observation in bin 0, so one count equals N and H = 0 up to the
+    rounding of log N - N log N / N; a count that wrapped would give about
+    log N) and whose other frequencies spread the observations; M = 1 (one
+    bin holding all N at every frequency), 3 and 10 (eight frequencies per
+    thread)."""
+    rng = np.random.default_rng([92, N])
+    t = np.sort(rng.uniform(0.0, 1000.0, N))
+    freqs = np.concatenate([[0.0], np.linspace(0.05, 30.0, 1499)])
+    ctx = G.Context(0)
+    for M in (1, 3, 10):
+        H = torch.empty(freqs.size, dtype=torch.float32, device="cuda")
+        G.fpw_phase_entropy(ctx, None, torch.from_numpy(t).cuda(), torch.from_numpy(freqs).cuda(), M, H)
+        torch.cuda.synchronize()
+        Hn = H.cpu().numpy().astype(np.float64)
+        assert abs(Hn[0]) < 2e-5
+        if M == 1:
+            assert np.all(np.abs(Hn) < 2e-5)
+        H_or = oracle.phase_entropy(t, freqs, M)
+        near = oracle.min_edge(t, freqs, M) <= 1e-9
+        err = np.abs(Hn - H_or)[~near]
+        assert err.max() < 2e-5, (M, err.max())
+    ctx.close()
