@@ -45,6 +45,12 @@ SMEM_EVALS_PER_CLK_SM = 8  # 16 B (A, B) read-modify-write per evaluation at 128
 KERNELS_PER_STEP = 5  # prep, tile_dev, tile, merge, latch
 SWEEP_MS = (10, 20, 50)  # bin counts of the throughput sweep
 ENTROPY_INST_PER_EVAL = 9.86  # thread instructions per evaluation of the dense phase-entropy kernel (ncu, M = 20)
+
+
+def entropy_R(M: int) -> int:
+    """Frequencies per thread of the dense phase-entropy kernel at M bins (the
+    library's launch rule)."""
+    return 8 if M <= 12 else (4 if M <= 24 else (2 if M <= 96 else 1))
 # DRAM bytes (read + write) of one tile-kernel launch at M = 20, from an ncu capture of a 1e4-curve sweep
 # batch over 2e4 frequencies (dram__bytes_read.sum + dram__bytes_write.sum). The kernel reads each curve
 # from DRAM once per launch (t and the staged weights, about 16.7 B per observation; per-tile re-reads
@@ -788,19 +794,28 @@ def run_configs_entropy(ctx, peak):
         torch.cuda.synchronize()
         ev = float(w.t.size) * w.nfreq
         rate = ev / (e0.elapsed_time(e1) / reps / 1e3)
-        smem_roof = 2.0 * peak  # 16 evaluations/clk/SM: a 4-byte count read-modify-write
+        # shared-memory term: per observation and warp, R count loads and R
+        # count stores of 4 B per lane (one wavefront each) plus the staged
+        # 16-byte record read by every lane (two wavefronts), over 32 R
+        # evaluations; the kernel's frequencies per thread R follow M
+        R = entropy_R(M)
+        smem_roof = peak / SMEM_EVALS_PER_CLK_SM * (32.0 * R / (2.0 * R + 2.0))
         issue_roof = peak / SMEM_EVALS_PER_CLK_SM * 128.0 / ENTROPY_INST_PER_EVAL
-        bind = min(smem_roof, issue_roof)
+        terms = {"smem": smem_roof}
+        if R == 4:  # the instruction mix was measured at R = 4 (M = 20)
+            terms["issue"] = issue_roof
+        binding = min(terms, key=terms.get)
         print(json.dumps({"config": f"single_ztf times (N={w.t.size}), dense phase entropy, M={M}, "
                                     f"{w.nfreq:.0e} freqs 0.01-100 1/d", "evals": ev,
                           "ms_per_call": e0.elapsed_time(e1) / reps, "evals_per_s_call": rate,
-                          "roofline": {"smem_count_rmw": smem_roof, "issue": issue_roof,
-                                       "binding": "issue" if issue_roof < smem_roof else "smem",
-                                       "frac_binding": rate / bind, "frac_smem": rate / smem_roof},
+                          "roofline": {"smem_counts_and_record": smem_roof, "issue": terms.get("issue"),
+                                       "binding": binding, "frac_binding": rate / terms[binding],
+                                       "frac_smem": rate / smem_roof, "R": R},
                           "status": ctx.status(),
-                          "note": f"roof terms: a 4 B count read-modify-write per evaluation (16 evals/clk/SM); "
+                          "note": f"roof terms: R count read-modify-writes (4 B per lane) and one 16 B broadcast "
+                                  f"record per observation and warp, 2 R + 2 wavefronts per 32 R evaluations; "
                                   f"128 thread instructions/clk/SM over {ENTROPY_INST_PER_EVAL} instructions per "
-                                  f"evaluation (ncu, M = 20)"}),
+                                  f"evaluation (ncu, M = 20, R = 4)"}),
               flush=True)
     r = L.make("ragged_10k")
     d = [torch.from_numpy(a).cuda() for a in (r.offsets, r.t, r.x, r.sigma, r.freqs)]

@@ -123,3 +123,35 @@ def test_autotuner_installs_shapes_and_keeps_parity(G):
         check_topk(idx[c], Sk[c], o_idx[c], o_S[c], o_dense=S_or[c], abs_tol=1e-7 * s_bound(x, s))
     ctx.clear_shapes()
     ctx.close()
+
+
+def test_autotuner_on_a_workload_sample_keeps_parity(G):
+    """tune_batch times shapes on a size-stratified sample of the batch's own
+    curves and installs one entry per M for batches of its typical size; the
+    call that then looks the shape up still matches the oracle."""
+    from paper_2502_00243_gb300 import autotune
+    ctx = G.Context(0)
+    w = L.ragged(41, [1200, 60, 2500, 333, 900, 45, 1800, 700], 3000, M=20, k=5)
+    entries = autotune.tune_batch(ctx, w.offsets, w.t, w.x, w.sigma, float(w.freqs[0]), float(w.freqs[-1]), (20, 50),
+                                  sample_curves=6, nfreq=4000, candidates=((128, 5), (128, 2), (64, 8)),
+                                  schedules=((0, 8), (128, 4)))
+    nt = autotune.n_typical(w.offsets)
+    assert sorted(e["M"] for e in entries) == [20, 50]
+    for e in entries:
+        assert e["M_lo"] == e["M_hi"] == e["M"] and e["n_lo"] <= nt < e["n_hi"] and e["geval_s"] > 0
+        assert e["sample_curves"] == 6
+    e20 = next(e for e in entries if e["M"] == 20)
+    idx, Sk, Sd, st = run_batch(ctx, w, dense=True)
+    assert st == 0
+    T, R, NC, _ = ctx.last_shape()
+    assert (T, R) == (e20["threads"], e20["freqs_per_thread"])
+    if e20["obs_chunk"]:
+        assert NC == e20["obs_chunk"]
+    S_or, o_idx, o_S = oracle.fpw_batch(w.offsets, w.t, w.x, w.sigma, w.freqs, 20, k=9)
+    for c in range(w.ncurves):
+        t, x, s = w.curve(c)
+        near = oracle.min_edge(t, w.freqs, 20) <= 1e-9
+        assert_S_close(Sd[c], S_or[c], s_bound(x, s), mask=~near, what=f"tuned curve {c}")
+        check_topk(idx[c], Sk[c], o_idx[c], o_S[c], o_dense=S_or[c], abs_tol=1e-7 * s_bound(x, s))
+    ctx.clear_shapes()
+    ctx.close()
