@@ -22,6 +22,17 @@ constexpr double kGridTolCycles = 2e-10;
 // Largest number of derived bin counts computed from one M_max pass.
 constexpr int kMaxGroups = 8;
 
+// Several-M calls whose (M_max, groups) have a compiled combination in the
+// tile kernel (1: M_max = 60 with groups 3, 6, 15; 2: 40 with 2, 4, 10; 3: 20
+// with 1, 2, 4; groups in that order), else 0 (the generic combination).
+inline int multi_spec_of(int M, int ngroups, const int* g) {
+  if (ngroups != 3) return 0;
+  if (M == 60 && g[0] == 3 && g[1] == 6 && g[2] == 15) return 1;
+  if (M == 40 && g[0] == 2 && g[1] == 4 && g[2] == 10) return 2;
+  if (M == 20 && g[0] == 1 && g[1] == 2 && g[2] == 4) return 3;
+  return 0;
+}
+
 // One unit of persistent work: frequencies [f_lo, f_hi) of curve `curve`.
 // Its top-k candidates go to row `slot` of the candidate table.
 struct WorkItem {
@@ -133,7 +144,7 @@ struct TileShape {
 // ---- launch wrappers (defined in the .cu files) -------------------------
 size_t tile_smem_bytes(int T, int R, int M, int NC, int k, int accum, int ngroups = 0);
 int tile_max_blocks_per_sm(int R, int phase_mode, int accum, int T, size_t smem, bool multi = false,
-                           bool dump = false);
+                           bool dump = false, int spec = 0);  // spec: the several-M combination (fpw_tile.cuh)
 bool tile_supported_R(int R);                      // some tile kernel has R frequencies per thread
 bool tile_has_R(int R, int accum, bool multi);     // the kernel for this sum mode / several-M call has it
 // Launches the kernel for (R, phase, accum); several-M when a.ngroups > 0, the

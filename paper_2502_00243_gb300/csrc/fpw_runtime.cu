@@ -559,7 +559,7 @@ int run_tile_path(fpw_ctx* ctx, const BatchCall& b) {
   int rc = choose_shape(ctx, b.p, b.M, b.k, max_n, n_typ, b.ngroups, sh);
   if (rc != FPW_OK) return rc;
   const int bps = tile_max_blocks_per_sm(sh.R, b.p.phase_mode, b.p.accum, sh.threads, sh.smem, b.ngroups > 0,
-                                         b.bins_out != nullptr);
+                                         b.bins_out != nullptr, multi_spec_of(b.M, b.ngroups, b.groups));
   if (bps < 1) return FPW_ENOTSUP;
   Plan* pl = get_plan(ctx, b.off_h, b.C, b.F, sh, bps, b.stream, &rc);
   if (!pl) return rc;

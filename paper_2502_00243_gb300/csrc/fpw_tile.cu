@@ -36,8 +36,8 @@ __global__ void tile_dev_kernel(const double* freqs, int64_t F, int W, int64_t t
   }
 }
 
-const void* pick(int R, int phase_mode, int accum, bool multi, bool dump) {
-  if (multi) return dump ? nullptr : tile_fn_multi(R, phase_mode);
+const void* pick(int R, int phase_mode, int accum, bool multi, bool dump, int spec = 0) {
+  if (multi) return dump ? nullptr : tile_fn_multi(R, phase_mode, spec);
   switch (accum) {
     case FPW_ACCUM_FP32:
       return (R == 3 || R == 5 || R == 6) ? tile_fn_f32_odd(R, phase_mode, dump) : tile_fn_f32(R, phase_mode, dump);
@@ -76,15 +76,17 @@ cudaError_t tile_init_attributes(int max_smem) {
               cudaFuncSetAttribute(pick(R, ph, acc, false, dump), cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
           if (e != cudaSuccess) return e;
         }
-      cudaError_t e = cudaFuncSetAttribute(pick(R, ph, FPW_ACCUM_FP32, true, false),
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
-      if (e != cudaSuccess) return e;
+      for (int spec = 0; spec <= 3; ++spec) {  // the generic kernel where no compiled one exists
+        cudaError_t e = cudaFuncSetAttribute(pick(R, ph, FPW_ACCUM_FP32, true, false, spec),
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+        if (e != cudaSuccess) return e;
+      }
     }
   return cudaSuccess;
 }
 
-int tile_max_blocks_per_sm(int R, int phase_mode, int accum, int T, size_t smem, bool multi, bool dump) {
-  const void* fn = pick(R, phase_mode, accum, multi, dump);
+int tile_max_blocks_per_sm(int R, int phase_mode, int accum, int T, size_t smem, bool multi, bool dump, int spec) {
+  const void* fn = pick(R, phase_mode, accum, multi, dump, spec);
   if (!fn) return 0;
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, T, smem) != cudaSuccess) return 0;
@@ -100,7 +102,8 @@ cudaError_t launch_tile_dev(const double* freqs, int64_t F, int W, int64_t tiles
 }
 
 cudaError_t launch_tile(const TileArgs& a, const TileShape& s, int phase_mode, int accum, int grid, cudaStream_t st) {
-  const void* fn = pick(s.R, phase_mode, accum, a.ngroups > 0, a.bins_out != nullptr);
+  const void* fn = pick(s.R, phase_mode, accum, a.ngroups > 0, a.bins_out != nullptr,
+                        multi_spec_of(a.M, a.ngroups, a.group_g));
   if (!fn) return cudaErrorInvalidValue;
   void* params[] = {const_cast<TileArgs*>(&a)};
   return cudaLaunchKernel(fn, dim3(grid), dim3(s.threads), params, s.smem, st);

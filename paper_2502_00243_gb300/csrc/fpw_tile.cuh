@@ -57,7 +57,7 @@ const void* tile_fn_f32(int R, int phase_mode, bool dump);
 const void* tile_fn_f32_odd(int R, int phase_mode, bool dump);  // R = 3, 5, 6
 const void* tile_fn_f64(int R, int phase_mode, bool dump);
 const void* tile_fn_comp(int R, int phase_mode, bool dump);
-const void* tile_fn_multi(int R, int phase_mode);
+const void* tile_fn_multi(int R, int phase_mode, int spec);  // spec: multi_spec_of(), 0 = generic
 
 struct TileLayout {
   size_t bins, pd, aw, candS, candI, topS, topI, edges, red, misc, total;
@@ -700,8 +700,130 @@ __global__ void __launch_bounds__(512, 1) tile_kernel(const TileArgs args) {
 // registers (72-114) instead of spilling them, which it did at 40 registers
 // under a 512-thread bound.
 constexpr int kMultiMaxThreads = 256;
+// Several-M combinations compiled for one M_max and three groups: the ones
+// Section 3.4 suggests (M_max = 60 or 40, giving M = 20, 10 and 4) and the
+// M = 20, 10, 5 split of M_max = 20. SPEC 0 is the generic combination.
+template <int SPEC>
+struct MultiSpec;
+template <>
+struct MultiSpec<1> {
+  static constexpr int MX = 60, G0 = 3, G1 = 6, G2 = 15;
+};
+template <>
+struct MultiSpec<2> {
+  static constexpr int MX = 40, G0 = 2, G1 = 4, G2 = 10;
+};
+template <>
+struct MultiSpec<3> {
+  static constexpr int MX = 20, G0 = 1, G1 = 2, G2 = 4;
+};
 
-template <int R, int PHASE>
+// One group's windows at bin m of the fixed combination: the window that ends
+// at m, [m - g + 1, m], belongs to offset (m + 1) mod g; its sum is Q_m minus
+// the prefix before its start (zero for the first window of offset 0).
+template <int G, int M, int MX>
+__device__ __forceinline__ void fixed_window(const float2 (&Q)[MX], float (&acc)[G], float cal) {
+  if constexpr (M >= G) {
+    acc[(M + 1) % G] += bin_term(f2sub(Q[M], Q[M - G]), cal);
+  } else if constexpr (M == G - 1) {
+    acc[0] += bin_term(f2sub(Q[M], make_float2(0.f, 0.f)), cal);
+  }
+}
+
+// The wrapping window of each offset o >= 1, [M_max - g + o, M_max - 1] and
+// [0, o - 1], added after the others; then the best offset (ties to the lower).
+template <int G, int MX>
+__device__ __forceinline__ void fixed_finish(const float2 (&Q)[MX], float (&acc)[G], float cal, float& best,
+                                             int& bo) {
+  const float2 total = Q[MX - 1];
+#pragma unroll
+  for (int o = 1; o < G; ++o) acc[o] += bin_term(bin_add(f2sub(total, Q[MX - G + o - 1]), Q[o - 1]), cal);
+  best = -INFINITY;
+  bo = 0;
+#pragma unroll
+  for (int o = 0; o < G; ++o)
+    if (acc[o] > best) {
+      best = acc[o];
+      bo = o;
+    }
+}
+
+template <int MX, int G0, int G1, int G2, int M>
+__device__ __forceinline__ void fixed_step(float2 (&Q)[MX], float2 v, float2& run, float (&a0)[G0], float (&a1)[G1],
+                                           float (&a2)[G2], float cal) {
+  run = bin_add(run, v);
+  Q[M] = run;
+  fixed_window<G0, M, MX>(Q, a0, cal);
+  fixed_window<G1, M, MX>(Q, a1, cal);
+  fixed_window<G2, M, MX>(Q, a2, cal);
+}
+
+template <int MX, int G0, int G1, int G2, int C, int U>
+__device__ __forceinline__ void fixed_chunk(float2 (&Q)[MX], const float2 (&v)[4], float2& run, float (&a0)[G0],
+                                            float (&a1)[G1], float (&a2)[G2], float cal) {
+  if constexpr (U < 4) {
+    fixed_step<MX, G0, G1, G2, C * 4 + U>(Q, v[U], run, a0, a1, a2, cal);
+    fixed_chunk<MX, G0, G1, G2, C, U + 1>(Q, v, run, a0, a1, a2, cal);
+  }
+}
+
+// Chunk C of four bins: the next chunk's bins are loaded before this chunk's
+// bins are cleared, so the loads of two chunks are in flight together.
+template <int MX, int G0, int G1, int G2, int C>
+__device__ __forceinline__ void fixed_chunks(float2* col, int st, float2 (&Q)[MX], float2 (&v)[4], float2& run,
+                                             float (&a0)[G0], float (&a1)[G1], float (&a2)[G2], float cal) {
+  if constexpr (C < MX / 4) {
+    float2 vn[4];
+    if constexpr (C + 1 < MX / 4) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) vn[u] = col[((C + 1) * 4 + u) * st];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) col[(C * 4 + u) * st] = make_float2(0.f, 0.f);
+    fixed_chunk<MX, G0, G1, G2, C, 0>(Q, v, run, a0, a1, a2, cal);
+    if constexpr (C + 1 < MX / 4) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = vn[u];
+    }
+    fixed_chunks<MX, G0, G1, G2, C + 1>(col, st, Q, v, run, a0, a1, a2, cal);
+  }
+}
+
+// Several-M combination of one slot's M_max bins for a compiled (M_max, groups):
+// one pass reads each bin once, clears it, forms the inclusive prefix sums Q_m
+// in registers and adds every window that ends at bin m to its offset's sum;
+// the windows that wrap past bin M_max - 1 are added last. The windows, terms
+// and order of additions are those of the generic combination (in-place prefix
+// sums, then per group and offset the windows in order, the wrapping one last),
+// so S is the same bit for bit, while each bin costs one shared-memory read and
+// one store instead of a read-modify-write for the prefix sums, a read per
+// group and a clearing store.
+template <int SPEC>
+__device__ __forceinline__ void combine_fixed(float2* col, int st, float cal, float (&best)[3], int (&bo)[3]) {
+  using SP = MultiSpec<SPEC>;
+  constexpr int MX = SP::MX, G0 = SP::G0, G1 = SP::G1, G2 = SP::G2;
+  static_assert(MX % 4 == 0 && MX % G0 == 0 && MX % G1 == 0 && MX % G2 == 0, "groups must divide M_max");
+  float2 Q[MX];
+  float a0[G0], a1[G1], a2[G2];
+#pragma unroll
+  for (int o = 0; o < G0; ++o) a0[o] = 0.f;
+#pragma unroll
+  for (int o = 0; o < G1; ++o) a1[o] = 0.f;
+#pragma unroll
+  for (int o = 0; o < G2; ++o) a2[o] = 0.f;
+  float2 v[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) v[u] = col[u * st];
+  float2 run = make_float2(0.f, 0.f);
+  fixed_chunks<MX, G0, G1, G2, 0>(col, st, Q, v, run, a0, a1, a2, cal);
+  fixed_finish<G0, MX>(Q, a0, cal, best[0], bo[0]);
+  fixed_finish<G1, MX>(Q, a1, cal, best[1], bo[1]);
+  fixed_finish<G2, MX>(Q, a2, cal, best[2], bo[2]);
+}
+
+
+
+template <int R, int PHASE, int SPEC>
 __global__ void __launch_bounds__(kMultiMaxThreads, 2) tile_kernel_multi(const TileArgs args) {
   using P = AccF32;
   using A = float;
@@ -740,72 +862,8 @@ __global__ void __launch_bounds__(kMultiMaxThreads, 2) tile_kernel_multi(const T
       accumulate_tile<R, PHASE, P, false>(args, b, s, a, fa, lin, resident && staged_lin && lin, staged_lin, base,
                                           n, wi);
 
-      // inclusive prefix sums Q[m] of the M_max bins, in place, per r; eight
-      // bins are loaded before any of them is stored back, so the loads of a
-      // chunk are in flight together (the bins of one thread form a dependent
-      // chain otherwise: a load cannot pass the previous bin's store)
-      float2 total[R];
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        A2* col = reinterpret_cast<A2*>(b.my_bins + (size_t)r * b.MT8);
-        const int st = b.T;  // stride between bins, in A2 units
-        A2 run = make_float2(0.f, 0.f);
-        int m = 0;
-        for (; m + 8 <= Mx; m += 8) {
-          A2 v[8];
-#pragma unroll
-          for (int u = 0; u < 8; ++u) v[u] = col[(m + u) * st];
-#pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            run = bin_add(run, v[u]);
-            col[(m + u) * st] = run;
-          }
-        }
-        for (; m < Mx; ++m) {
-          run = bin_add(run, col[m * st]);
-          col[m * st] = run;
-        }
-        total[r] = run;
-      }
-      for (int g = 0; g < ng; ++g) {
-        const int gs = args.group_g[g], Mg = Mx / gs;
-        A S[R];
-        int off[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-          const A2* col = reinterpret_cast<const A2*>(b.my_bins + (size_t)r * b.MT8);
-          const int st = b.T;
-          A best = (A)-INFINITY;
-          int bo = 0;
-          for (int o = 0; o < gs; ++o) {
-            A acc = (A)0;
-            // window j spans bins [j gs + o, j gs + o + gs - 1]: its sum is
-            // Q[end] - Q[start - 1], and its end is the next window's start - 1,
-            // so one prefix value is read per window (carried in `prev`)
-            const A2 q0 = (o > 0) ? col[(o - 1) * st] : make_float2(0.f, 0.f);
-            A2 prev = q0;
-            // the windows that end below bin M_max: independent loads (no
-            // stores here), unrolled so that they issue together; the terms
-            // are added in window order
-            const int nin = (o > 0) ? Mg - 1 : Mg;
-            const A2* e = col + (size_t)(o + gs - 1) * st;
-#pragma unroll 4
-            for (int j = 0; j < nin; ++j) {
-              const A2 q = e[(size_t)j * gs * st];
-              acc += bin_term(f2sub(q, prev), cal);
-              prev = q;
-            }
-            // o >= 1: the last window wraps past bin M_max - 1 and ends at o - 1
-            if (o > 0) acc += bin_term(bin_add(f2sub(total[r], prev), q0), cal);
-            if (acc > best) {
-              best = acc;
-              bo = o;
-            }
-          }
-          const int64_t k = s + (int64_t)b.j0 + r;
-          S[r] = (k >= 0 && k < F) ? best : (A)-INFINITY;
-          off[r] = bo;
-        }
+      // the reported S of group g per owned frequency, and the peaks
+      auto emit = [&](int g, const A (&S)[R], const int (&off)[R]) {
         if (args.S_out) {
 #pragma unroll
           for (int r = 0; r < R; ++r) {
@@ -816,12 +874,100 @@ __global__ void __launch_bounds__(kMultiMaxThreads, 2) tile_kernel_multi(const T
           }
         }
         if (b.kk > 0) tile_peaks<R, P>(args, b, S, off, 6, s, wi, b.topS + g * FPW_MAX_TOPK, b.topI + g * FPW_MAX_TOPK);
-      }
-      // clear the bins for the next tile
+      };
+      if constexpr (SPEC != 0) {
+        // compiled (M_max, groups): one pass per slot, bins cleared on the way
+        A Sg[3][R];
+        int offg[3][R];
+#pragma unroll 1
+        for (int r = 0; r < R; ++r) {  // one slot at a time: the pass holds its prefix sums in registers
+          float best[3];
+          int bo[3];
+          combine_fixed<SPEC>(reinterpret_cast<A2*>(b.my_bins + (size_t)r * b.MT8), b.T, cal, best, bo);
+          const int64_t k = s + (int64_t)b.j0 + r;
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        A2* col = reinterpret_cast<A2*>(b.my_bins + (size_t)r * b.MT8);
-        for (int m = 0; m < Mx; ++m) col[m * b.T] = make_float2(0.f, 0.f);
+          for (int q = 0; q < 3; ++q) {
+            Sg[q][r] = (k >= 0 && k < F) ? best[q] : (A)-INFINITY;
+            offg[q][r] = bo[q];
+          }
+        }
+#pragma unroll
+        for (int g = 0; g < 3; ++g) emit(g, Sg[g], offg[g]);
+      } else {
+        // inclusive prefix sums Q[m] of the M_max bins, in place, per r; eight
+        // bins are loaded before any of them is stored back, so the loads of a
+        // chunk are in flight together (the bins of one thread form a dependent
+        // chain otherwise: a load cannot pass the previous bin's store)
+        float2 total[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          A2* col = reinterpret_cast<A2*>(b.my_bins + (size_t)r * b.MT8);
+          const int st = b.T;  // stride between bins, in A2 units
+          A2 run = make_float2(0.f, 0.f);
+          int m = 0;
+          for (; m + 8 <= Mx; m += 8) {
+            A2 v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = col[(m + u) * st];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              run = bin_add(run, v[u]);
+              col[(m + u) * st] = run;
+            }
+          }
+          for (; m < Mx; ++m) {
+            run = bin_add(run, col[m * st]);
+            col[m * st] = run;
+          }
+          total[r] = run;
+        }
+        for (int g = 0; g < ng; ++g) {
+          const int gs = args.group_g[g], Mg = Mx / gs;
+          A S[R];
+          int off[R];
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            const A2* col = reinterpret_cast<const A2*>(b.my_bins + (size_t)r * b.MT8);
+            const int st = b.T;
+            A best = (A)-INFINITY;
+            int bo = 0;
+            for (int o = 0; o < gs; ++o) {
+              A acc = (A)0;
+              // window j spans bins [j gs + o, j gs + o + gs - 1]: its sum is
+              // Q[end] - Q[start - 1], and its end is the next window's start - 1,
+              // so one prefix value is read per window (carried in `prev`)
+              const A2 q0 = (o > 0) ? col[(o - 1) * st] : make_float2(0.f, 0.f);
+              A2 prev = q0;
+              // the windows that end below bin M_max: independent loads (no
+              // stores here), unrolled so that they issue together; the terms
+              // are added in window order
+              const int nin = (o > 0) ? Mg - 1 : Mg;
+              const A2* e = col + (size_t)(o + gs - 1) * st;
+#pragma unroll 4
+              for (int j = 0; j < nin; ++j) {
+                const A2 q = e[(size_t)j * gs * st];
+                acc += bin_term(f2sub(q, prev), cal);
+                prev = q;
+              }
+              // o >= 1: the last window wraps past bin M_max - 1 and ends at o - 1
+              if (o > 0) acc += bin_term(bin_add(f2sub(total[r], prev), q0), cal);
+              if (acc > best) {
+                best = acc;
+                bo = o;
+              }
+            }
+            const int64_t k = s + (int64_t)b.j0 + r;
+            S[r] = (k >= 0 && k < F) ? best : (A)-INFINITY;
+            off[r] = bo;
+          }
+          emit(g, S, off);
+        }
+        // clear the bins for the next tile
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          A2* col = reinterpret_cast<A2*>(b.my_bins + (size_t)r * b.MT8);
+          for (int m = 0; m < Mx; ++m) col[m * b.T] = make_float2(0.f, 0.f);
+        }
       }
       __syncthreads();
     }

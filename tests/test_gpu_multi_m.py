@@ -163,3 +163,28 @@ def test_long_curve_peaks_merged_by_a_block(G):
                     col = So[:, mi[c, q, j]]
                     assert abs(col[mo[c, q, j]] - col.max()) <= 1e-4 * abs(col.max()) + 1e-6 * bound
     ctx.close()
+
+
+@pytest.mark.parametrize("M_max,groups,ns,F", [
+    (60, [3, 6, 15], [1300, 45, 2600, 700], 3001),
+    (40, [2, 4, 10], [900, 2000, 77], 2500),
+    (20, [1, 2, 4], [1500, 300, 2900], 4099),
+])
+def test_compiled_combination_equals_generic_bitwise(G, M_max, groups, ns, F):
+    """(M_max, groups) = (60; 3, 6, 15), (40; 2, 4, 10) and (20; 1, 2, 4), in that
+    order, run a combination compiled for them (one pass over the bins with
+    the prefix sums in registers); the same groups in reverse order run the
+    generic one. Same windows, terms and order of additions: the dense S, the
+    peaks and their offsets must agree bit for bit, with and without a
+    nonzero 1/alpha^2."""
+    w = L.ragged(90 + M_max, ns, F, M=M_max, k=5)
+    ctx = G.Context(0)
+    for inv_a2 in (0.0, 0.7):
+        p = G.fpw_params_default(inv_alpha2=inv_a2)
+        i1, o1, s1, d1 = run_multi(G, ctx, w, M_max, groups, 5, params=p)
+        i2, o2, s2, d2 = run_multi(G, ctx, w, M_max, groups[::-1], 5, params=p)
+        assert np.array_equal(d1, d2[:, ::-1], equal_nan=True)
+        assert np.array_equal(i1, i2[:, ::-1]) and np.array_equal(o1, o2[:, ::-1])
+        assert np.array_equal(s1, s2[:, ::-1], equal_nan=True)
+        assert np.isfinite(d1).all() and (i1[:, :, 0] >= 0).all()
+    ctx.close()
