@@ -56,7 +56,7 @@ def entropy_R(M: int) -> int:
 # from DRAM once per launch (t and the staged weights, about 16.7 B per observation; per-tile re-reads
 # hit L2), so a full launch adds only the larger grid (8 B per extra frequency). Valid only for the
 # kernel source it was measured on (sha256 prefix of the tile-kernel sources, tile_source_hash).
-TILE_TRAFFIC = {"source_sha256_16": "325a7d36c6e15ac1", "bytes": 143.20e6, "nfreq": 20_000}
+TILE_TRAFFIC = {"source_sha256_16": "ce9276e3f4830ec5", "bytes": 142.63e6, "nfreq": 20_000}
 
 
 # ---------------------------------------------------------------- workload generation (spawned workers)
