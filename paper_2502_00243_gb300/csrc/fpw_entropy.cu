@@ -16,7 +16,7 @@ namespace fpw {
 namespace {
 
 constexpr int kEntThreads = 128;
-constexpr int kEntChunk = 512;
+constexpr int kEntChunk = 256;
 
 // H from bin counts: log N - (1/N) sum_m N_m log N_m, in FP32 (the count
 // terms are exact integers; the logarithms carry the rounding).
